@@ -1,0 +1,59 @@
+"""Shape of the synthetic workloads: gate counts of the QFT and random-layer
+circuits and the determinism of the seeded generators."""
+import os
+
+from tqs_inputs import (batch_circuits_spec, qft, random_layers, read_text, write_text,
+                        inverse_qft_on_fourier_state, splitmix64)
+
+
+def test_qft_gate_counts():
+    for n in (10, 16, 20, 26):
+        c = qft(n)
+        n1, n2 = c.counts()
+        assert n1 == n and n2 == n * (n - 1) // 2 + n // 2
+    assert len(qft(20)) == 220
+
+
+def test_random_layer_counts_and_determinism():
+    c = random_layers(16, 40, 16040)
+    assert c.counts() == (640, 320)
+    assert random_layers(16, 40, 16040).gates == c.gates
+    assert random_layers(16, 40, 16041).gates != c.gates
+    assert random_layers(26, 30, 26030).counts() == (780, 390)
+    odd = random_layers(5, 2, 1)
+    assert odd.counts() == (10, 4)
+    for name, q0, q1, th, _ in c.gates:
+        if name == "cz":
+            assert q0 != q1
+        else:
+            assert name in ("rx", "ry", "rz") and 0.0 <= th < 6.2832
+
+
+def test_batch_spec_ranges():
+    spec = batch_circuits_spec()
+    assert len(spec) == 64
+    assert all(12 <= n <= 22 and 20 <= L <= 60 for n, L, _ in spec)
+    assert spec == batch_circuits_spec()
+    assert len({(n, L) for n, L, _ in spec}) > 30
+
+
+def test_inverse_qft_counts():
+    n1, n2 = inverse_qft_on_fourier_state(20, 5).counts()
+    assert n1 == 60 and n2 == 200  # 20 H + 20 P (prep), 20 H; 190 CP + 10 SWAP
+
+
+def test_text_round_trip(tmp_path):
+    c = random_layers(6, 3, 9)
+    c.add("u1", 2, -1, 0.0, [[0, 1], [1, 0]])
+    p = os.path.join(tmp_path, "c.txt")
+    write_text(c, p)
+    d = read_text(p)
+    assert d.n == c.n and len(d.gates) == len(c.gates)
+    for a, b in zip(c.gates[:-1], d.gates[:-1]):
+        assert a[:4] == b[:4]
+
+
+def test_splitmix_below_range():
+    r = splitmix64(3)
+    vals = [r.below(7) for _ in range(5000)]
+    assert min(vals) == 0 and max(vals) == 6
