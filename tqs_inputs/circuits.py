@@ -155,7 +155,7 @@ def write_text(c: Circuit, path: str) -> None:
             extra = ""
             if mat is not None:
                 m = np.asarray(mat, dtype=complex).ravel()
-                extra = " " + " ".join(f"{v.real!r} {v.imag!r}" for v in m)
+                extra = " " + " ".join(f"{float(v.real)!r} {float(v.imag)!r}" for v in m)
             f.write(f"{name} {q0} {q1} {th!r}{extra}\n")
 
 
