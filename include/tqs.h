@@ -1,0 +1,211 @@
+/*
+ * tqs.h -- C ABI of the GB300 (sm_103a) noisy Monte-Carlo state-vector simulator
+ * with tree-based reuse of intermediate states (TQSim, arXiv 2203.13892).
+ *
+ * The problem statement these calls follow (Sec. 2.4, 3.1, 3.2):
+ *   a circuit (ordered gate list on n qubits) is run for N noisy shots; after every
+ *   gate a depolarizing noise site may insert a random Pauli on that gate's
+ *   qubits; each shot ends in a measurement whose bits may flip (readout error).
+ *   The baseline simulator runs every shot from |0...0>.  Tree mode partitions the
+ *   circuit into k+1 subcircuits with arities (A_0..A_k): instance m of level i
+ *   starts from the stored state of its parent m / A_i, so intermediate states are
+ *   reused by A_i children (Sec. 3.1, Eq. circuit-instances read as
+ *   M_i = prod_{j<=i} A_j); the leaves are the N measured outcomes.
+ *
+ * Conventions
+ *   - qubit q is bit q of the amplitude index and of the histogram bin;
+ *   - two-qubit matrices act on the local index k = bit(q0) + 2*bit(q1);
+ *     for CX, q0 is the control;
+ *   - the noise site after gate g is numbered g (0-based, gate order); its
+ *     Pauli is drawn with Philox4x32-10 keyed by the seed and the counter
+ *     (node_lo, node_hi, g, 1); an error occurs iff word0 < floor(p*2^32); the
+ *     Pauli index is 1 + (word1 * npaulis) >> 32 with npaulis = 3 (X,Y,Z) for
+ *     one-qubit and 15 for two-qubit gates (index t -> P_{t>>2} on q0 and
+ *     P_{t&3} on q1, with I,X,Y,Z = 0..3);
+ *   - leaf m is measured with u = ((w0>>5)*2^26 + (w1>>6)) * 2^-53 drawn from
+ *     counter (m_lo, m_hi, 0, 2): the outcome is the smallest y whose running sum
+ *     of |psi_y|^2 exceeds u * sum|psi|^2; bit q then flips iff the word0 of
+ *     counter (m_lo, m_hi, q, 3) is below floor(pm*2^32).
+ *
+ * Errors: every call returns a tqs_status and leaves its outputs untouched on
+ * error; tqs_last_error() gives a thread-local message for the last failure.
+ * Handles are owned by the library until their destroy call; every buffer
+ * passed in is owned by the caller.  Device-side failures are reported as
+ * TQS_ECUDA (or TQS_ETIMEOUT for a bounded wait that gave up); no kernel traps.
+ */
+#ifndef TQS_PUBLIC_API_H_
+#define TQS_PUBLIC_API_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TQS_ABI_VERSION 1
+#define TQS_MAX_LEVELS 17
+#define TQS_MAX_QUBITS 30
+
+typedef enum {
+    TQS_OK = 0,
+    TQS_EINVAL = 1,       /* malformed argument (qubit out of range, p outside [0,1], ...) */
+    TQS_ENOMEM = 2,       /* host or device allocation failed / workspace too small */
+    TQS_ECUDA = 3,        /* a CUDA call failed (message in tqs_last_error) */
+    TQS_ETIMEOUT = 4,     /* a bounded device wait gave up */
+    TQS_EUNSUPPORTED = 5  /* valid request outside what this build supports */
+} tqs_status;
+
+typedef enum {
+    TQS_H = 0, TQS_X, TQS_Y, TQS_Z, TQS_S, TQS_SDG, TQS_T, TQS_TDG,
+    TQS_RX, TQS_RY, TQS_RZ, TQS_P,
+    TQS_CX, TQS_CZ, TQS_CP, TQS_SWAP,
+    TQS_U1, /* arbitrary 2x2 matrix in `mat` */
+    TQS_U2  /* arbitrary 4x4 matrix in `mat` */
+} tqs_gate_kind;
+
+/* One gate.  theta is used by RX/RY/RZ/P/CP; mat (interleaved re,im, row-major,
+ * 2x2 for U1 and 4x4 for U2) is read only for U1/U2 and may be NULL otherwise.
+ * q1 is ignored for one-qubit gates.  The matrix is copied at creation. */
+typedef struct {
+    uint32_t kind, q0, q1;
+    double theta;
+    const double *mat;
+} tqs_gate;
+
+typedef struct tqs_circuit tqs_circuit; /* opaque, library-owned */
+typedef struct tqs_noise tqs_noise;     /* opaque, library-owned */
+typedef struct tqs_plan tqs_plan;       /* opaque, library-owned */
+
+/* Circuit from an ordered gate list (Sec. 2.2).  n_qubits in [1, TQS_MAX_QUBITS];
+ * n_gates may be 0.  EINVAL on an unknown kind, a qubit >= n_qubits, q0 == q1
+ * for a two-qubit gate, a non-finite angle or a NULL matrix for U1/U2. */
+tqs_status tqs_circuit_create(uint32_t n_qubits, const tqs_gate *gates, size_t n_gates,
+                              tqs_circuit **out);
+void tqs_circuit_destroy(tqs_circuit *c);
+
+/* Noise model (Sec. 4.3): depolarizing probability p1 after one-qubit gates, p2
+ * after two-qubit gates (probability of a non-identity Pauli, uniform over the
+ * 3 or 15 choices), readout bit-flip probability pm.  Each in [0,1] else EINVAL. */
+tqs_status tqs_noise_model(double p1, double p2, double pm, tqs_noise **out);
+void tqs_noise_destroy(tqs_noise *nz);
+
+typedef enum { TQS_MODE_BASELINE = 0, TQS_MODE_TREE = 1 } tqs_mode;
+typedef enum { TQS_FP64 = 0, TQS_FP32 = 1 } tqs_precision;
+typedef enum {
+    TQS_PART_DCP = 0,      /* dynamic circuit partition (Sec. 3.2) */
+    TQS_PART_UCP = 1,      /* uniform: k+1 levels of equal arity (Sec. 3.2.1) */
+    TQS_PART_XCP = 2,      /* exponential: A_i = a * 2^(k-i) (Sec. 3.2.1) */
+    TQS_PART_EXPLICIT = 3, /* caller's arity[] and split[] */
+    TQS_PART_LEARNED = 4   /* reserved: currently EUNSUPPORTED */
+} tqs_partitioner;
+
+#define TQS_FLAG_NO_FIDELITY 0x1u /* skip the ideal run and the fidelity (fidelity = NaN) */
+#define TQS_FLAG_PROFILE 0x2u     /* time every launch with CUDA events (report.prof_*) */
+
+/* Kernel classes timed under TQS_FLAG_PROFILE (index into report.prof_*). */
+#define TQS_PROF_NOISE 0   /* Philox noise draws + Pauli frames */
+#define TQS_PROF_STORE 1   /* tile pass that stores the node state */
+#define TQS_PROF_SUMS 2    /* leaf tile pass that writes measurement block sums */
+#define TQS_PROF_SAMPLE 3  /* per-leaf outcome pick + tile recompute */
+#define TQS_PROF_KINDS 4
+
+/* Options.  A zeroed struct is NOT the default: call tqs_options_default().
+ *   z, eps       DCP confidence z and margin eps (defaults 1.96, 0.05)
+ *   copy_gates   DCP minimum subcircuit length c in gates (default 10, Sec. 3.6)
+ *   k            number of levels - 1 for UCP/XCP/EXPLICIT (levels = k+1 <= 17)
+ *   arity, split EXPLICIT tree: arity[0..k], split[0..k+1] with split[0] = 0,
+ *                split[k+1] = n_gates, non-decreasing; prod(arity) >= shots
+ *   tile_qubits  maximum shared-memory tile width t in [6, 13] (0 = default: 12 FP32, 11 FP64)
+ *   batch        node instances per launch (0 = chosen from the memory budget)
+ *   workspace, workspace_bytes   optional caller-owned DEVICE buffer (>= 256-byte
+ *                aligned) used for all scratch; NULL = the library allocates
+ *   stream       cudaStream_t to run on (NULL = legacy default stream)
+ *   flags        TQS_FLAG_* bits */
+typedef struct {
+    tqs_mode mode;
+    tqs_precision prec;
+    tqs_partitioner part;
+    double z, eps;
+    uint32_t copy_gates;
+    uint32_t k;
+    const uint64_t *arity;
+    const uint32_t *split;
+    uint32_t tile_qubits;
+    uint32_t batch;
+    void *workspace;
+    size_t workspace_bytes;
+    void *stream;
+    uint32_t flags;
+} tqs_options;
+
+void tqs_options_default(tqs_options *o);
+
+/* Filled by tqs_simulate / tqs_plan_execute when non-NULL. */
+typedef struct {
+    uint64_t shots_done;
+    uint32_t levels;                      /* k + 1 */
+    uint64_t arity[TQS_MAX_LEVELS];
+    uint32_t split[TQS_MAX_LEVELS + 1];
+    uint64_t node_instances[TQS_MAX_LEVELS]; /* nodes simulated per level */
+    uint32_t passes[TQS_MAX_LEVELS];         /* state passes per node per level */
+    uint64_t kernel_launches;
+    double kernel_ms;         /* device time of the simulation (CUDA events) */
+    double shots_per_s;       /* shots_done / kernel_ms */
+    double alg_bytes;         /* algorithmic state bytes moved (2 per stored node, 1 per leaf) */
+    double fid_norm, fid_s;   /* normalized fidelity F and F_s vs the ideal run (NaN if skipped/undefined) */
+    double theo_speedup;      /* levels * N / sum_i node_instances[i] */
+    /* per kernel class (TQS_PROF_*), filled under TQS_FLAG_PROFILE: launches,
+     * summed event time and algorithmic bytes (state reads + writes; a state is
+     * 2^n amplitudes of 8 (FP32) or 16 (FP64) bytes) */
+    uint64_t prof_launches[TQS_PROF_KINDS];
+    double prof_ms[TQS_PROF_KINDS];
+    double prof_bytes[TQS_PROF_KINDS];
+} tqs_report;
+
+/* Partition only (host, no GPU): the tree the options select for `shots`.
+ * arity_out[TQS_MAX_LEVELS], split_out[TQS_MAX_LEVELS+1]; *levels_out = k+1. */
+tqs_status tqs_partition(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots,
+                         const tqs_options *opts, uint32_t *levels_out, uint64_t *arity_out,
+                         uint32_t *split_out);
+
+/* Full simulation: plan, upload, run on the GPU, copy the histogram back.
+ * counts: caller-owned HOST array of 2^n uint64 (overwritten; sums to shots).
+ * fidelity: normalized fidelity F vs the noiseless run (NaN with TQS_OK when the
+ * ideal distribution is uniform, or when TQS_FLAG_NO_FIDELITY is set). */
+tqs_status tqs_simulate(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, uint64_t seed,
+                        const tqs_options *opts, uint64_t *counts, double *fidelity,
+                        tqs_report *report);
+
+/* Device-resident execution (what a benchmark times): tqs_plan_create does the
+ * host planning and uploads gate tables and workspace; tqs_plan_execute runs one
+ * simulation with `seed`, accumulating into the caller's DEVICE array d_counts
+ * (2^n uint64, zeroed by the call) on opts->stream, and returns without
+ * synchronising (report fields needing the device are filled only when
+ * `report` is non-NULL, which synchronises). */
+tqs_status tqs_plan_create(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots,
+                           const tqs_options *opts, tqs_plan **out);
+tqs_status tqs_plan_execute(tqs_plan *p, uint64_t seed, uint64_t *d_counts, tqs_report *report);
+size_t tqs_plan_workspace_bytes(const tqs_plan *p);
+void tqs_plan_destroy(tqs_plan *p);
+
+/* Debug / parity entry points.
+ * tqs_debug_node_state: the logical state (2^n complex, interleaved FP64, HOST
+ * array) of instance `node` of tree level `level` after its subcircuit, in the
+ * tree the options select, including the global phase of the inserted Paulis.
+ * tqs_debug_node_noise: the Pauli index (0 = none) drawn at each site of that
+ * node's subcircuit (HOST array of split[level+1]-split[level] bytes). */
+tqs_status tqs_debug_node_state(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots,
+                                uint64_t seed, const tqs_options *opts, uint32_t level,
+                                uint64_t node, double *psi_out);
+tqs_status tqs_debug_node_noise(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots,
+                                uint64_t seed, const tqs_options *opts, uint32_t level,
+                                uint64_t node, uint8_t *paulis_out);
+
+const char *tqs_last_error(void);
+int tqs_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TQS_PUBLIC_API_H_ */

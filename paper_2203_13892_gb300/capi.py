@@ -1,0 +1,295 @@
+"""ctypes binding of libtqs (include/tqs.h): same names, argument marshalling only.
+
+Every step of the simulation runs in the CUDA library; this module converts
+Python values to the C structs and back.  Importing it loads ``_build/libtqs.so``
+(building it with nvcc first if it is missing) and raises if that fails: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+TQS_OK, TQS_EINVAL, TQS_ENOMEM, TQS_ECUDA, TQS_ETIMEOUT, TQS_EUNSUPPORTED = range(6)
+TQS_MODE_BASELINE, TQS_MODE_TREE = 0, 1
+TQS_FP64, TQS_FP32 = 0, 1
+TQS_PART_DCP, TQS_PART_UCP, TQS_PART_XCP, TQS_PART_EXPLICIT, TQS_PART_LEARNED = range(5)
+TQS_FLAG_NO_FIDELITY = 0x1
+TQS_FLAG_PROFILE = 0x2
+TQS_MAX_LEVELS = 17
+TQS_PROF_KINDS = 4
+PROF_NAMES = ("noise", "store", "sums", "sample")
+
+GATE_KINDS = {
+    "h": 0, "x": 1, "y": 2, "z": 3, "s": 4, "sdg": 5, "t": 6, "tdg": 7,
+    "rx": 8, "ry": 9, "rz": 10, "p": 11, "cx": 12, "cz": 13, "cp": 14, "swap": 15,
+    "u1": 16, "u2": 17,
+}
+_TWO = {"cx", "cz", "cp", "swap", "u2"}
+
+
+class TqsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tqs status {status}: {msg}")
+        self.status = status
+
+
+class tqs_gate(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("q0", C.c_uint32), ("q1", C.c_uint32),
+                ("theta", C.c_double), ("mat", C.POINTER(C.c_double))]
+
+
+class tqs_options(C.Structure):
+    _fields_ = [("mode", C.c_int), ("prec", C.c_int), ("part", C.c_int),
+                ("z", C.c_double), ("eps", C.c_double), ("copy_gates", C.c_uint32),
+                ("k", C.c_uint32), ("arity", C.POINTER(C.c_uint64)), ("split", C.POINTER(C.c_uint32)),
+                ("tile_qubits", C.c_uint32), ("batch", C.c_uint32), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t), ("stream", C.c_void_p), ("flags", C.c_uint32)]
+
+
+class tqs_report(C.Structure):
+    _fields_ = [("shots_done", C.c_uint64), ("levels", C.c_uint32),
+                ("arity", C.c_uint64 * TQS_MAX_LEVELS), ("split", C.c_uint32 * (TQS_MAX_LEVELS + 1)),
+                ("node_instances", C.c_uint64 * TQS_MAX_LEVELS), ("passes", C.c_uint32 * TQS_MAX_LEVELS),
+                ("kernel_launches", C.c_uint64), ("kernel_ms", C.c_double), ("shots_per_s", C.c_double),
+                ("alg_bytes", C.c_double), ("fid_norm", C.c_double), ("fid_s", C.c_double),
+                ("theo_speedup", C.c_double), ("prof_launches", C.c_uint64 * TQS_PROF_KINDS),
+                ("prof_ms", C.c_double * TQS_PROF_KINDS), ("prof_bytes", C.c_double * TQS_PROF_KINDS)]
+
+    def as_dict(self) -> dict:
+        L = self.levels
+        return {
+            "shots_done": self.shots_done, "levels": L,
+            "arity": list(self.arity[:L]), "split": list(self.split[:L + 1]),
+            "node_instances": list(self.node_instances[:L]), "passes": list(self.passes[:L]),
+            "kernel_launches": self.kernel_launches, "kernel_ms": self.kernel_ms,
+            "shots_per_s": self.shots_per_s, "alg_bytes": self.alg_bytes,
+            "fid_norm": self.fid_norm, "fid_s": self.fid_s, "theo_speedup": self.theo_speedup,
+            "prof": {PROF_NAMES[k]: {"launches": self.prof_launches[k], "ms": self.prof_ms[k],
+                                     "bytes": self.prof_bytes[k]} for k in range(TQS_PROF_KINDS)},
+        }
+
+
+_lock = threading.Lock()
+_lib = None
+
+# Exported symbols, by header declaration.
+EXPORTS = (
+    "tqs_circuit_create", "tqs_circuit_destroy", "tqs_noise_model", "tqs_noise_destroy",
+    "tqs_options_default", "tqs_partition", "tqs_simulate", "tqs_plan_create",
+    "tqs_plan_execute", "tqs_plan_workspace_bytes", "tqs_plan_destroy",
+    "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_last_error", "tqs_abi_version",
+)
+
+
+def lib():
+    """The loaded libtqs (built in-tree on first use)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                path = _build.build()
+            L = C.CDLL(path)
+            vp, u64p, u32p, dp = C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32), C.POINTER(C.c_double)
+            st = C.c_int
+            L.tqs_circuit_create.argtypes = [C.c_uint32, C.POINTER(tqs_gate), C.c_size_t, C.POINTER(vp)]
+            L.tqs_circuit_create.restype = st
+            L.tqs_circuit_destroy.argtypes = [vp]
+            L.tqs_noise_model.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(vp)]
+            L.tqs_noise_model.restype = st
+            L.tqs_noise_destroy.argtypes = [vp]
+            L.tqs_options_default.argtypes = [C.POINTER(tqs_options)]
+            L.tqs_partition.argtypes = [vp, vp, C.c_uint64, C.POINTER(tqs_options), u32p, u64p, u32p]
+            L.tqs_partition.restype = st
+            L.tqs_simulate.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.POINTER(tqs_options), u64p, dp,
+                                       C.POINTER(tqs_report)]
+            L.tqs_simulate.restype = st
+            L.tqs_plan_create.argtypes = [vp, vp, C.c_uint64, C.POINTER(tqs_options), C.POINTER(vp)]
+            L.tqs_plan_create.restype = st
+            L.tqs_plan_execute.argtypes = [vp, C.c_uint64, vp, C.POINTER(tqs_report)]
+            L.tqs_plan_execute.restype = st
+            L.tqs_plan_workspace_bytes.argtypes = [vp]
+            L.tqs_plan_workspace_bytes.restype = C.c_size_t
+            L.tqs_plan_destroy.argtypes = [vp]
+            L.tqs_debug_node_state.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.POINTER(tqs_options),
+                                               C.c_uint32, C.c_uint64, dp]
+            L.tqs_debug_node_state.restype = st
+            L.tqs_debug_node_noise.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.POINTER(tqs_options),
+                                               C.c_uint32, C.c_uint64, C.POINTER(C.c_uint8)]
+            L.tqs_debug_node_noise.restype = st
+            L.tqs_last_error.restype = C.c_char_p
+            L.tqs_abi_version.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != TQS_OK:
+        raise TqsError(status, lib().tqs_last_error().decode())
+
+
+def tqs_last_error() -> str:
+    return lib().tqs_last_error().decode()
+
+
+def tqs_abi_version() -> int:
+    return int(lib().tqs_abi_version())
+
+
+class Handle:
+    """Owns a library handle and destroys it on close/garbage collection."""
+
+    def __init__(self, ptr, destroy):
+        self.ptr = ptr
+        self._destroy = destroy
+
+    def close(self):
+        if self.ptr:
+            self._destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def tqs_circuit_create(n: int, gates) -> Handle:
+    """gates: tqs_inputs-style tuples (name, q0, q1, theta, mat)."""
+    G = len(gates)
+    arr = (tqs_gate * max(G, 1))()
+    keep = []
+    for i, (name, q0, q1, th, mat) in enumerate(gates):
+        arr[i].kind = GATE_KINDS[name]
+        arr[i].q0 = int(q0)
+        arr[i].q1 = int(q1) if name in _TWO else 0
+        arr[i].theta = float(th)
+        if mat is not None:
+            z = np.asarray(mat, dtype=complex).ravel()
+            buf = np.empty(2 * len(z), dtype=np.float64)
+            buf[0::2], buf[1::2] = z.real, z.imag
+            keep.append(buf)
+            arr[i].mat = buf.ctypes.data_as(C.POINTER(C.c_double))
+    out = C.c_void_p()
+    _check(lib().tqs_circuit_create(int(n), arr, G, C.byref(out)))
+    return Handle(out.value, lib().tqs_circuit_destroy)
+
+
+def circuit(c) -> Handle:
+    """tqs_circuit from a tqs_inputs.Circuit."""
+    return tqs_circuit_create(c.n, c.gates)
+
+
+def tqs_circuit_destroy(h: Handle) -> None:
+    h.close()
+
+
+def tqs_noise_model(p1: float, p2: float, pm: float) -> Handle:
+    out = C.c_void_p()
+    _check(lib().tqs_noise_model(float(p1), float(p2), float(pm), C.byref(out)))
+    return Handle(out.value, lib().tqs_noise_destroy)
+
+
+def tqs_noise_destroy(h: Handle) -> None:
+    h.close()
+
+
+def tqs_options_default() -> tqs_options:
+    o = tqs_options()
+    lib().tqs_options_default(C.byref(o))
+    return o
+
+
+def options(mode: str = "tree", prec: str = "fp32", part: str = "dcp", arity: Optional[Sequence[int]] = None,
+            split: Optional[Sequence[int]] = None, k: int = 0, **kw) -> tqs_options:
+    """Build a tqs_options from keywords.  Arrays passed for an explicit tree are
+    kept alive on the returned struct."""
+    o = tqs_options_default()
+    o.mode = {"baseline": TQS_MODE_BASELINE, "tree": TQS_MODE_TREE}[mode]
+    o.prec = {"fp64": TQS_FP64, "fp32": TQS_FP32}[prec]
+    o.part = {"dcp": TQS_PART_DCP, "ucp": TQS_PART_UCP, "xcp": TQS_PART_XCP,
+              "explicit": TQS_PART_EXPLICIT, "learned": TQS_PART_LEARNED}[part]
+    o.k = int(k)
+    if arity is not None:
+        a = np.ascontiguousarray(arity, dtype=np.uint64)
+        s = np.ascontiguousarray(split, dtype=np.uint32)
+        o._keep = (a, s)
+        o.arity = a.ctypes.data_as(C.POINTER(C.c_uint64))
+        o.split = s.ctypes.data_as(C.POINTER(C.c_uint32))
+        o.k = len(a) - 1
+        o.part = TQS_PART_EXPLICIT
+    for key, v in kw.items():
+        setattr(o, key, v)
+    return o
+
+
+def tqs_partition(c: Handle, nz: Handle, shots: int, opts: Optional[tqs_options] = None) -> Tuple[list, list]:
+    L = C.c_uint32()
+    a = (C.c_uint64 * TQS_MAX_LEVELS)()
+    s = (C.c_uint32 * (TQS_MAX_LEVELS + 1))()
+    _check(lib().tqs_partition(c.ptr, nz.ptr, int(shots), C.byref(opts) if opts else None, C.byref(L), a, s))
+    return list(a[:L.value]), list(s[:L.value + 1])
+
+
+def tqs_simulate(c: Handle, nz: Handle, shots: int, seed: int, opts: Optional[tqs_options] = None,
+                 n: Optional[int] = None):
+    """Returns (counts uint64[2^n] on the host, normalised fidelity, report dict)."""
+    if n is None:
+        raise ValueError("n (qubit count) is required to size the histogram")
+    counts = np.zeros(1 << n, dtype=np.uint64)
+    fid = C.c_double()
+    rep = tqs_report()
+    _check(lib().tqs_simulate(c.ptr, nz.ptr, int(shots), int(seed), C.byref(opts) if opts else None,
+                              counts.ctypes.data_as(C.POINTER(C.c_uint64)), C.byref(fid), C.byref(rep)))
+    return counts, fid.value, rep.as_dict()
+
+
+def tqs_plan_create(c: Handle, nz: Handle, shots: int, opts: Optional[tqs_options] = None) -> Handle:
+    out = C.c_void_p()
+    _check(lib().tqs_plan_create(c.ptr, nz.ptr, int(shots), C.byref(opts) if opts else None, C.byref(out)))
+    return Handle(out.value, lib().tqs_plan_destroy)
+
+
+def tqs_plan_execute(plan: Handle, seed: int, d_counts: int, report: bool = False):
+    rep = tqs_report() if report else None
+    _check(lib().tqs_plan_execute(plan.ptr, int(seed), C.c_void_p(int(d_counts)),
+                                  C.byref(rep) if rep is not None else None))
+    return rep.as_dict() if rep is not None else None
+
+
+def tqs_plan_workspace_bytes(plan: Handle) -> int:
+    return int(lib().tqs_plan_workspace_bytes(plan.ptr))
+
+
+def tqs_plan_destroy(plan: Handle) -> None:
+    plan.close()
+
+
+def tqs_debug_node_state(c: Handle, nz: Handle, shots: int, seed: int, opts: Optional[tqs_options],
+                         level: int, node: int, n: int) -> np.ndarray:
+    out = np.zeros(2 << n, dtype=np.float64)
+    _check(lib().tqs_debug_node_state(c.ptr, nz.ptr, int(shots), int(seed), C.byref(opts) if opts else None,
+                                      int(level), int(node), out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out[0::2] + 1j * out[1::2]
+
+
+def tqs_debug_node_noise(c: Handle, nz: Handle, shots: int, seed: int, opts: Optional[tqs_options],
+                         level: int, node: int, sites: int) -> np.ndarray:
+    out = np.zeros(max(sites, 1), dtype=np.uint8)
+    _check(lib().tqs_debug_node_noise(c.ptr, nz.ptr, int(shots), int(seed), C.byref(opts) if opts else None,
+                                      int(level), int(node), out.ctypes.data_as(C.POINTER(C.c_uint8))))
+    return out[:sites]

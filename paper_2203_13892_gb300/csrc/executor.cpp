@@ -1,0 +1,389 @@
+// executor.cpp -- device plan (workspace layout, uploads) and the tree traversal
+// that launches the kernels: depth-first over the tree in chunks of `batch`
+// sibling-consecutive node instances per level (Sec. 3.1), so the live state
+// pool is one chunk per level.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "executor.h"
+
+namespace tqs {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+std::string cuda_msg(const char *what, int err)
+{
+    return std::string(what) + ": " + cudaGetErrorString((cudaError_t)err);
+}
+
+#define CK(call)                                                        \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) {                                        \
+            err = cuda_msg(#call, (int)e_);                             \
+            return TQS_ECUDA;                                           \
+        }                                                               \
+    } while (0)
+#define CKL(call)                                                       \
+    do {                                                                \
+        int e_ = (call);                                                \
+        launches++;                                                     \
+        if (e_ != 0) {                                                  \
+            err = cuda_msg(#call, e_);                                  \
+            return TQS_ECUDA;                                           \
+        }                                                               \
+    } while (0)
+// A launch of kernel class `kind` moving `bytes` algorithmic bytes, bracketed by
+// CUDA events on the plan's stream when profiling.
+#define CKP(kind, bytes, call)                                          \
+    do {                                                                \
+        cudaEvent_t a_ = nullptr, b_ = nullptr;                         \
+        if (profiling()) {                                              \
+            a_ = next_event();                                          \
+            b_ = next_event();                                          \
+            if (a_) cudaEventRecord(a_, stream);                        \
+        }                                                               \
+        CKL(call);                                                      \
+        if (a_ && b_) {                                                 \
+            cudaEventRecord(b_, stream);                                \
+            prof.push_back(ProfRec{(kind), (bytes), a_, b_});           \
+        }                                                               \
+    } while (0)
+
+DevicePlan::~DevicePlan() { release(); }
+
+cudaEvent_t DevicePlan::next_event()
+{
+    if (ev_used == ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess)
+            return nullptr;
+        ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+}
+
+void DevicePlan::release()
+{
+    for (cudaEvent_t e : ev_pool)
+        cudaEventDestroy(e);
+    ev_pool.clear();
+    if (own_ws && ws)
+        cudaFree(ws);
+    ws = nullptr;
+    own_ws = false;
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    ev0 = ev1 = nullptr;
+}
+
+// Workspace layout for `B` slots per level.
+size_t DevicePlan::layout(uint64_t B, bool assign)
+{
+    const PlanHost &H = host;
+    const uint32_t L = (uint32_t)H.levels.size();
+    const size_t esz = H.prec == TQS_FP64 ? 16 : 8;
+    const size_t sbytes = ((size_t)1 << H.n) * esz;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    size_t o_instr = take(sizeof(Instr) * std::max<size_t>(H.instrs.size(), 1));
+    size_t o_mats = take((H.prec == TQS_FP64 ? 8 : 4) * H.mats64.size());
+    size_t o_pst = take(sizeof(uint32_t) * (H.passes.size() + L) + 64);
+    size_t o_fid = take(sizeof(double) * (3 + 3 * 256));
+    size_t o_perm = take(32);
+    size_t o_counts = take(sizeof(uint64_t) * ((size_t)1 << H.n));
+    std::vector<size_t> o_state(L), o_noise(L), o_meta(L);
+    for (uint32_t i = 0; i < L; i++) {
+        const Level &lv = H.levels[i];
+        const uint32_t np = lv.pass_end - lv.pass_begin;
+        const bool leaf = i + 1 == L;
+        const bool needs_state = !leaf || np > 1 || store_leaves;
+        o_state[i] = needs_state ? take(sbytes * B) : (size_t)-1;
+        o_noise[i] = take(std::max<size_t>(lv.g1 - lv.g0, 1) * B);
+        o_meta[i] = take(sizeof(NodeMeta) * (np + 1) * B);
+    }
+    size_t o_S = take(sizeof(double) * H.samp.groups * B);
+    if (assign) {
+        char *b = (char *)ws;
+        d_instr = (Instr *)(b + o_instr);
+        d_mats = b + o_mats;
+        d_pass_start = (uint32_t *)(b + o_pst);
+        d_fid = (double *)(b + o_fid);
+        d_perm = (uint8_t *)(b + o_perm);
+        d_counts_internal = (unsigned long long *)(b + o_counts);
+        state.assign(L, nullptr);
+        noise.assign(L, nullptr);
+        meta.assign(L, nullptr);
+        for (uint32_t i = 0; i < L; i++) {
+            state[i] = o_state[i] == (size_t)-1 ? nullptr : (void *)(b + o_state[i]);
+            noise[i] = (uint8_t *)(b + o_noise[i]);
+            meta[i] = (NodeMeta *)(b + o_meta[i]);
+        }
+        d_S = (double *)(b + o_S);
+    }
+    return off;
+}
+
+tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
+{
+    opts = o;
+    stream = (cudaStream_t)o.stream;
+    const PlanHost &H = host;
+    // state bytes of one slot across all levels (for the batch choice)
+    size_t fixed = layout(0, false);
+    size_t per_slot = layout(1, false) - fixed + 256 * 8;
+    uint64_t maxact = 1;
+    for (auto &lv : H.levels)
+        maxact = std::max<uint64_t>(maxact, lv.active);
+    const uint64_t tiles = (uint64_t)1 << (H.n - std::min<uint32_t>(H.n, H.tile_max));
+    uint64_t want = o.batch ? o.batch : std::max<uint64_t>(64, 65536 / tiles);
+    want = std::min<uint64_t>(want, 65535);
+    want = std::min<uint64_t>(want, maxact);
+    size_t budget;
+    if (o.workspace) {
+        budget = o.workspace_bytes > fixed ? o.workspace_bytes - fixed : 0;
+    } else {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        budget = (size_t)(0.75 * (double)fr);
+        budget = budget > fixed ? budget - fixed : 0;
+    }
+    uint64_t B = std::min<uint64_t>(want, budget / std::max<size_t>(per_slot, 1));
+    if (B == 0) {
+        err = "workspace too small for one node per level (" + std::to_string(fixed + per_slot) + " bytes needed)";
+        return TQS_ENOMEM;
+    }
+    batch = B;
+    ws_bytes = layout(B, false);
+    if (o.workspace) {
+        if (((uintptr_t)o.workspace & 255) != 0) {
+            err = "workspace must be 256-byte aligned";
+            return TQS_EINVAL;
+        }
+        ws = o.workspace;
+        own_ws = false;
+    } else {
+        CK(cudaMalloc(&ws, ws_bytes));
+        own_ws = true;
+    }
+    layout(B, true);
+    // uploads
+    CK(cudaMemcpyAsync(d_instr, H.instrs.data(), sizeof(Instr) * H.instrs.size(), cudaMemcpyHostToDevice, stream));
+    if (H.prec == TQS_FP64)
+        CK(cudaMemcpyAsync(d_mats, H.mats64.data(), 8 * H.mats64.size(), cudaMemcpyHostToDevice, stream));
+    else
+        CK(cudaMemcpyAsync(d_mats, H.mats32.data(), 4 * H.mats32.size(), cudaMemcpyHostToDevice, stream));
+    // per level: pass start sites (npass + 1 entries), concatenated
+    pst_host.clear();
+    pst_off.clear();
+    for (auto &lv : H.levels) {
+        pst_off.push_back((uint32_t)pst_host.size());
+        for (uint32_t p = lv.pass_begin; p < lv.pass_end; p++)
+            pst_host.push_back(H.passes[p].site_begin);
+        pst_host.push_back(lv.g1 - lv.g0);
+    }
+    CK(cudaMemcpyAsync(d_pass_start, pst_host.data(), 4 * pst_host.size(), cudaMemcpyHostToDevice, stream));
+    uint8_t perm[32] = {0};
+    for (uint32_t q = 0; q < H.n; q++)
+        perm[q] = H.levels.back().perm[q];
+    CK(cudaMemcpyAsync(d_perm, perm, 32, cudaMemcpyHostToDevice, stream));
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+    CK(cudaStreamSynchronize(stream));
+    return TQS_OK;
+}
+
+tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vector<uint64_t> &plo,
+                                 uint64_t seed, unsigned long long *counts, std::string &err)
+{
+    const PlanHost &H = host;
+    const Level &lv = H.levels[i];
+    const uint32_t L = (uint32_t)H.levels.size();
+    const uint32_t np = lv.pass_end - lv.pass_begin;
+    const uint64_t nn = hi - lo;
+    plo[i] = lo;
+    node_count[i] += nn;
+    NoiseLaunch nl;
+    nl.instr = d_instr + H.passes[lv.pass_begin].ibeg;
+    nl.sites = lv.g1 - lv.g0;
+    nl.pass_start = d_pass_start + pst_off[i];
+    nl.npass = np;
+    nl.node_lo = lo;
+    nl.nnodes = nn;
+    nl.parent_meta = i ? meta[i - 1] : nullptr;
+    nl.parent_stride = i ? (H.levels[i - 1].pass_end - H.levels[i - 1].pass_begin + 1) : 0;
+    nl.parent_end = i ? nl.parent_stride - 1 : 0;
+    nl.parent_lo = i ? plo[i - 1] : 0;
+    nl.arity = lv.arity;
+    nl.noise_out = noise[i];
+    nl.meta_out = meta[i];
+    nl.seed = seed;
+    nl.thr1 = H.thr1;
+    nl.thr2 = H.thr2;
+    CKP(TQS_PROF_NOISE, (double)nn * (nl.sites + 8.0 * (np + 1)), launch_noise(nl, stream));
+    const bool leaf = (i + 1 == L) && !store_leaves;
+    const double sb = (double)((size_t)1 << H.n) * (H.prec == TQS_FP64 ? 16 : 8);
+    for (uint32_t pl = 0; pl < np; pl++) {
+        const Pass &ps = H.passes[lv.pass_begin + pl];
+        PassLaunch a;
+        std::memset(&a, 0, sizeof(a));
+        a.fp64 = H.prec == TQS_FP64;
+        a.in = pl == 0 ? (i ? state[i - 1] : nullptr) : state[i];
+        a.in_from_parent = (pl == 0 && i > 0) ? 1 : 0;
+        a.out = state[i];
+        a.state_elems = (uint64_t)1 << H.n;
+        a.node_lo = lo;
+        a.parent_lo = i ? plo[i - 1] : 0;
+        a.arity = lv.arity;
+        a.nnodes = (uint32_t)nn;
+        a.instr = d_instr;
+        a.ibeg = ps.ibeg;
+        a.iend = ps.iend;
+        a.n = H.n;
+        a.t = ps.t;
+        a.L = ps.L;
+        std::memcpy(a.tbits, ps.tbits, sizeof(a.tbits));
+        std::memcpy(a.hbits, ps.hbits, sizeof(a.hbits));
+        a.mats = d_mats;
+        a.noise = noise[i];
+        a.sites = lv.g1 - lv.g0;
+        a.meta = meta[i];
+        a.meta_stride = np + 1;
+        a.pass_local = pl;
+        a.S = d_S;
+        a.samp = &H.samp;
+        a.counts = counts;
+        a.seed = seed;
+        a.thrm = H.thrm;
+        // state bytes a pass must move: read its input (nothing when it starts
+        // from |0...0>) and, unless it only measures, write its output
+        const double rd = a.in ? sb : 0.0;
+        if (leaf && pl + 1 == np) {
+            const double sums = 8.0 * (double)H.samp.groups;
+            a.mode = MODE_SUMS;
+            CKP(TQS_PROF_SUMS, (double)nn * (rd + sums), launch_pass(a, stream));
+            a.mode = MODE_SAMPLE;
+            const double blk = rd / (double)((uint64_t)1 << (H.n - ps.t));
+            CKP(TQS_PROF_SAMPLE, (double)nn * (sums + blk), launch_pass(a, stream));
+            alg_bytes += (double)nn * rd;
+        } else {
+            a.mode = MODE_STORE;
+            CKP(TQS_PROF_STORE, (double)nn * (rd + sb), launch_pass(a, stream));
+            alg_bytes += (double)nn * (rd + sb);
+        }
+    }
+    if (i + 1 < L) {
+        const Level &ch = H.levels[i + 1];
+        const uint64_t clo = lo * ch.arity;
+        const uint64_t chi = std::min<uint64_t>(hi * ch.arity, ch.active);
+        for (uint64_t c = clo; c < chi; c += batch) {
+            tqs_status st = run_level(i + 1, c, std::min<uint64_t>(c + batch, chi), plo, seed, counts, err);
+            if (st != TQS_OK)
+                return st;
+        }
+    }
+    return TQS_OK;
+}
+
+tqs_status DevicePlan::execute(uint64_t seed, unsigned long long *counts, bool timed, std::string &err)
+{
+    const PlanHost &H = host;
+    const uint32_t L = (uint32_t)H.levels.size();
+    launches = 0;
+    alg_bytes = 0;
+    ev_used = 0;
+    prof.clear();
+    node_count.assign(L, 0);
+    std::vector<uint64_t> plo(L, 0);
+    if (timed)
+        CK(cudaEventRecord(ev0, stream));
+    CKL(launch_fill_u64(counts, (uint64_t)1 << H.n, stream));
+    const uint64_t roots = H.levels[0].active;
+    for (uint64_t lo = 0; lo < roots; lo += batch) {
+        tqs_status st = run_level(0, lo, std::min<uint64_t>(lo + batch, roots), plo, seed, counts, err);
+        if (st != TQS_OK)
+            return st;
+    }
+    if (timed)
+        CK(cudaEventRecord(ev1, stream));
+    return TQS_OK;
+}
+
+// State of one node along its ancestor chain (debug / ideal run): every level
+// runs as a chunk of one node, all passes store.
+tqs_status DevicePlan::run_chain(uint32_t level, uint64_t node, uint64_t seed, std::string &err)
+{
+    const PlanHost &H = host;
+    std::vector<uint64_t> chain(level + 1);
+    chain[level] = node;
+    for (int i = (int)level; i > 0; i--)
+        chain[i - 1] = chain[i] / H.levels[i].arity;
+    std::vector<uint64_t> plo(H.levels.size(), 0);
+    node_count.assign(H.levels.size(), 0);
+    for (uint32_t i = 0; i <= level; i++) {
+        // same as run_level but without descending and with stores only
+        const Level &lv = H.levels[i];
+        const uint32_t np = lv.pass_end - lv.pass_begin;
+        plo[i] = chain[i];
+        NoiseLaunch nl;
+        nl.instr = d_instr + H.passes[lv.pass_begin].ibeg;
+        nl.sites = lv.g1 - lv.g0;
+        nl.pass_start = d_pass_start + pst_off[i];
+        nl.npass = np;
+        nl.node_lo = chain[i];
+        nl.nnodes = 1;
+        nl.parent_meta = i ? meta[i - 1] : nullptr;
+        nl.parent_stride = i ? (H.levels[i - 1].pass_end - H.levels[i - 1].pass_begin + 1) : 0;
+        nl.parent_end = i ? nl.parent_stride - 1 : 0;
+        nl.parent_lo = i ? plo[i - 1] : 0;
+        nl.arity = lv.arity;
+        nl.noise_out = noise[i];
+        nl.meta_out = meta[i];
+        nl.seed = seed;
+        nl.thr1 = H.thr1;
+        nl.thr2 = H.thr2;
+        CKL(launch_noise(nl, stream));
+        for (uint32_t pl = 0; pl < np; pl++) {
+            const Pass &ps = H.passes[lv.pass_begin + pl];
+            PassLaunch a;
+            std::memset(&a, 0, sizeof(a));
+            a.mode = MODE_STORE;
+            a.fp64 = H.prec == TQS_FP64;
+            a.in = pl == 0 ? (i ? state[i - 1] : nullptr) : state[i];
+            a.in_from_parent = (pl == 0 && i > 0) ? 1 : 0;
+            a.out = state[i];
+            a.state_elems = (uint64_t)1 << H.n;
+            a.node_lo = chain[i];
+            a.parent_lo = i ? plo[i - 1] : 0;
+            a.arity = lv.arity;
+            a.nnodes = 1;
+            a.instr = d_instr;
+            a.ibeg = ps.ibeg;
+            a.iend = ps.iend;
+            a.n = H.n;
+            a.t = ps.t;
+            a.L = ps.L;
+            std::memcpy(a.tbits, ps.tbits, sizeof(a.tbits));
+            std::memcpy(a.hbits, ps.hbits, sizeof(a.hbits));
+            a.mats = d_mats;
+            a.noise = noise[i];
+            a.sites = lv.g1 - lv.g0;
+            a.meta = meta[i];
+            a.meta_stride = np + 1;
+            a.pass_local = pl;
+            a.seed = seed;
+            CKL(launch_pass(a, stream));
+        }
+    }
+    return TQS_OK;
+}
+
+}  // namespace tqs

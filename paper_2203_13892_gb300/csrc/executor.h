@@ -1,0 +1,58 @@
+// executor.h -- device-side plan: workspace carve-up, uploads and launches.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace tqs {
+
+std::string cuda_msg(const char *what, int err);
+
+struct DevicePlan {
+    PlanHost host;
+    tqs_options opts{};
+    cudaStream_t stream = nullptr;
+    bool store_leaves = false;  // keep leaf states (debug chains)
+    uint64_t batch = 0;         // node instances per chunk and level
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    Instr *d_instr = nullptr;
+    void *d_mats = nullptr;
+    uint32_t *d_pass_start = nullptr;
+    double *d_fid = nullptr;
+    uint8_t *d_perm = nullptr;
+    unsigned long long *d_counts_internal = nullptr;
+    double *d_S = nullptr;
+    std::vector<void *> state;
+    std::vector<uint8_t *> noise;
+    std::vector<NodeMeta *> meta;
+    std::vector<uint32_t> pst_host, pst_off;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // per-launch profiling (TQS_FLAG_PROFILE)
+    struct ProfRec { int kind; double bytes; cudaEvent_t a, b; };
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<ProfRec> prof;
+    cudaEvent_t next_event();
+    // statistics of the last execute
+    uint64_t launches = 0;
+    double alg_bytes = 0;
+    std::vector<uint64_t> node_count;
+
+    ~DevicePlan();
+    void release();
+    size_t layout(uint64_t B, bool assign);
+    tqs_status create(const tqs_options &o, std::string &err);
+    tqs_status execute(uint64_t seed, unsigned long long *counts, bool timed, std::string &err);
+    tqs_status run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vector<uint64_t> &plo,
+                         uint64_t seed, unsigned long long *counts, std::string &err);
+    tqs_status run_chain(uint32_t level, uint64_t node, uint64_t seed, std::string &err);
+    bool profiling() const { return (opts.flags & TQS_FLAG_PROFILE) != 0; }
+};
+
+}  // namespace tqs

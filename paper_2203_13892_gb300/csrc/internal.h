@@ -1,0 +1,179 @@
+// internal.h -- structures shared by the host planner, the executor and the CUDA
+// kernels of libtqs (not part of the public ABI; see include/tqs.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tqs.h"
+
+namespace tqs {
+
+constexpr int kThreads = 256;      // threads per CTA of every state kernel
+constexpr int kMaxTile = 13;       // largest shared-memory tile (2^13 amplitudes)
+constexpr int kMaxGamma = 8;       // sampler group = up to 2^8 consecutive outcomes
+constexpr uint32_t kDomNoise = 1, kDomMeas = 2, kDomRead = 3;
+
+// ---------------------------------------------------------------------------
+// Device-visible plan records
+// ---------------------------------------------------------------------------
+enum Op : uint8_t { OP_NOP = 0, OP_DENSE1 = 1, OP_DENSE2 = 2, OP_DIAG1 = 3, OP_DIAG2 = 4 };
+
+// One gate (and the noise site that follows it) lowered for one pass.
+struct Instr {
+    uint8_t op;
+    uint8_t j0, j1;      // tile positions of the gate qubits (dense ops)
+    uint8_t p0, p1;      // physical bits of the gate qubits
+    uint8_t np0, np1;    // physical bits of the noise site's qubits (a on np0, b on np1)
+    uint8_t npaulis;     // 3 (one-qubit site) or 15 (two-qubit site)
+    uint16_t site;       // site index relative to the level's first gate
+    uint16_t pad;
+    uint32_t gate;       // global gate index (row of the matrix tables)
+};
+static_assert(sizeof(Instr) == 16, "Instr layout");
+
+// Pauli frame of a node at a pass boundary: logical psi(x) = i^phase * phi(x ^ mask)
+// where phi is the stored vector (physical bit order).
+struct NodeMeta {
+    uint32_t mask;
+    uint32_t phase;
+};
+
+// ---------------------------------------------------------------------------
+// Host-side circuit and plan
+// ---------------------------------------------------------------------------
+struct Gate {
+    uint32_t kind, q0, q1;
+    double theta;
+    double m[32];  // interleaved complex matrix (2x2 or 4x4) in the local basis
+};
+
+struct Circuit {
+    uint32_t n;
+    std::vector<Gate> gates;
+};
+
+struct Noise {
+    double p1, p2, pm;
+};
+
+struct Pass {
+    uint32_t level;
+    uint32_t ibeg, iend;          // instruction range (global instruction list)
+    uint32_t site_begin;          // first site of the pass, relative to the level
+    uint32_t t, L;                // tile width and number of contiguous low bits
+    uint8_t tbits[kMaxTile];      // physical bit of each tile position (ascending)
+    uint8_t hbits[32];            // remaining physical bits (ascending), n - t of them
+};
+
+struct Level {
+    uint32_t g0, g1;              // gate range
+    uint64_t arity;               // A_i
+    uint64_t active;              // nodes simulated at this level
+    uint64_t below;               // prod_{j>i} A_j
+    uint32_t pass_begin, pass_end;
+    std::vector<uint8_t> perm;    // logical qubit -> physical bit after this level
+};
+
+// Measurement layout of the final pass: outcome y (logical) is grouped in blocks
+// of 2^gamma consecutive values whose low gamma logical bits all lie in the tile.
+struct SamplerLayout {
+    uint32_t gamma;
+    uint64_t groups;               // 2^(n - gamma) block sums per leaf
+    uint8_t phys_of_logical[32];   // P[q]
+    uint8_t rank_pos[kMaxTile];    // tile position of logical rank r (ascending logical bit)
+    uint8_t rank_q[kMaxTile];      // logical bit of rank r
+    uint8_t logical_of_hbit[32];   // logical bit of each non-tile physical bit
+    int8_t rank_of_logical[32];    // rank within the tile, or -1 if the bit is not in the tile
+};
+
+struct PlanHost {
+    uint32_t n;
+    tqs_precision prec;
+    tqs_mode mode;
+    uint64_t shots;
+    std::vector<Level> levels;
+    std::vector<Pass> passes;
+    std::vector<Instr> instrs;
+    std::vector<double> mats64;    // 32 doubles per gate
+    std::vector<float> mats32;     // 32 floats per gate
+    uint64_t thr1, thr2, thrm;     // floor(p * 2^32)
+    SamplerLayout samp;
+    uint32_t tile_max;
+};
+
+// Host planning (planner.cpp)
+std::string validate_and_build_circuit(uint32_t n, const tqs_gate *gates, size_t ng, Circuit &out);
+void gate_matrix(uint32_t kind, double theta, const double *mat, double *out);
+bool is_two_qubit(uint32_t kind);
+bool is_diagonal(uint32_t kind);
+std::string partition(const Circuit &c, const Noise &nz, uint64_t shots, const tqs_options &o,
+                      std::vector<uint64_t> &arity, std::vector<uint32_t> &split);
+std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const tqs_options &o,
+                       const std::vector<uint64_t> &arity, const std::vector<uint32_t> &split,
+                       PlanHost &p);
+uint64_t threshold32(double p);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (kernels.cu).  All return the cudaError_t of the launch as int.
+// ---------------------------------------------------------------------------
+struct DevTables {
+    const Instr *instr;
+    const void *mats;          // double[32*G] or float[32*G] by precision
+    const uint32_t *pass_site_begin;  // per global pass: first site (level-relative)
+};
+
+struct NoiseLaunch {
+    const Instr *instr;        // the level's instructions (one per site, in order)
+    uint32_t sites;            // sites in the level
+    const uint32_t *pass_start;// device: level-relative first site of each pass, npass+1 entries
+    uint32_t npass;
+    uint64_t node_lo, nnodes;  // global ids [node_lo, node_lo + nnodes)
+    const NodeMeta *parent_meta;  // nullptr for level 0
+    uint32_t parent_stride;    // NodeMeta entries per parent slot
+    uint32_t parent_end;       // index of the parent's final meta
+    uint64_t parent_lo, arity;
+    uint8_t *noise_out;        // [slot][sites]
+    NodeMeta *meta_out;        // [slot][npass + 1]
+    uint64_t seed, thr1, thr2;
+};
+int launch_noise(const NoiseLaunch &a, void *stream);
+
+enum PassMode { MODE_STORE = 0, MODE_SUMS = 1, MODE_SAMPLE = 2 };
+
+struct PassLaunch {
+    int mode;
+    int fp64;
+    const void *in;            // nullptr = synthesize |0...0>
+    int in_from_parent;        // 1: input slot = node / arity - parent_lo, 0: own slot
+    void *out;                 // STORE output states
+    uint64_t state_elems;      // 2^n
+    uint64_t node_lo, parent_lo, arity;
+    uint32_t nnodes;
+    const Instr *instr;
+    uint32_t ibeg, iend;
+    uint32_t n, t, L;
+    uint8_t tbits[kMaxTile];
+    uint8_t hbits[32];
+    const void *mats;
+    const uint8_t *noise;
+    uint32_t sites;
+    const NodeMeta *meta;
+    uint32_t meta_stride, pass_local;
+    double *S;                 // SUMS / SAMPLE block sums
+    const SamplerLayout *samp; // copied by value into the kernel parameters
+    unsigned long long *counts;
+    uint64_t seed, thrm;
+};
+int launch_pass(const PassLaunch &a, void *stream);
+
+int launch_fill_u64(unsigned long long *p, uint64_t n, void *stream);
+
+// Fidelity of a histogram against the ideal state (FP64 reductions on device).
+// ideal: stored physical-order ideal state; perm: logical -> physical.
+int launch_fidelity(const void *ideal, int fp64, const unsigned long long *counts, uint32_t n,
+                    const uint8_t *perm_dev, uint64_t shots, double *out3, void *stream);
+
+}  // namespace tqs

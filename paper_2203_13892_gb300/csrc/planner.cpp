@@ -1,0 +1,481 @@
+// planner.cpp -- host planning for the tree Monte-Carlo path:
+//   circuit validation and gate matrices (Sec. 2.2), circuit partitioners
+//   (DCP / UCP / XCP / explicit, Sec. 3.2 and 3.6), the noise-site table and
+//   the lowering of every subcircuit into shared-memory tile passes.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace tqs {
+
+bool is_two_qubit(uint32_t k)
+{
+    return k == TQS_CX || k == TQS_CZ || k == TQS_CP || k == TQS_SWAP || k == TQS_U2;
+}
+
+bool is_diagonal(uint32_t k)
+{
+    switch (k) {
+    case TQS_Z: case TQS_S: case TQS_SDG: case TQS_T: case TQS_TDG: case TQS_RZ: case TQS_P:
+    case TQS_CZ: case TQS_CP:
+        return true;
+    default:
+        return false;
+    }
+}
+
+uint64_t threshold32(double p)
+{
+    return (uint64_t)std::floor(p * 4294967296.0);
+}
+
+// Textbook matrices; interleaved (re, im), row-major; two-qubit gates act on the
+// local index k = bit(q0) + 2 bit(q1) with q0 the control of CX.
+void gate_matrix(uint32_t kind, double th, const double *mat, double *m)
+{
+    std::memset(m, 0, 32 * sizeof(double));
+    auto set = [&](int i, double re, double im) { m[2 * i] = re; m[2 * i + 1] = im; };
+    const double r = 1.0 / std::sqrt(2.0);
+    const double c = std::cos(th / 2), s = std::sin(th / 2);
+    switch (kind) {
+    case TQS_H: set(0, r, 0); set(1, r, 0); set(2, r, 0); set(3, -r, 0); break;
+    case TQS_X: set(1, 1, 0); set(2, 1, 0); break;
+    case TQS_Y: set(1, 0, -1); set(2, 0, 1); break;
+    case TQS_Z: set(0, 1, 0); set(3, -1, 0); break;
+    case TQS_S: set(0, 1, 0); set(3, 0, 1); break;
+    case TQS_SDG: set(0, 1, 0); set(3, 0, -1); break;
+    case TQS_T: set(0, 1, 0); set(3, r, r); break;
+    case TQS_TDG: set(0, 1, 0); set(3, r, -r); break;
+    case TQS_RX: set(0, c, 0); set(1, 0, -s); set(2, 0, -s); set(3, c, 0); break;
+    case TQS_RY: set(0, c, 0); set(1, -s, 0); set(2, s, 0); set(3, c, 0); break;
+    case TQS_RZ: set(0, std::cos(th / 2), -std::sin(th / 2)); set(3, std::cos(th / 2), std::sin(th / 2)); break;
+    case TQS_P: set(0, 1, 0); set(3, std::cos(th), std::sin(th)); break;
+    case TQS_U1: std::memcpy(m, mat, 8 * sizeof(double)); break;
+    case TQS_CX: set(0, 1, 0); set(1 * 4 + 3, 1, 0); set(2 * 4 + 2, 1, 0); set(3 * 4 + 1, 1, 0); break;
+    case TQS_CZ: set(0, 1, 0); set(5, 1, 0); set(10, 1, 0); set(15, -1, 0); break;
+    case TQS_CP: set(0, 1, 0); set(5, 1, 0); set(10, 1, 0); set(15, std::cos(th), std::sin(th)); break;
+    case TQS_SWAP: set(0, 1, 0); set(1 * 4 + 2, 1, 0); set(2 * 4 + 1, 1, 0); set(15, 1, 0); break;
+    case TQS_U2: std::memcpy(m, mat, 32 * sizeof(double)); break;
+    default: break;
+    }
+}
+
+std::string validate_and_build_circuit(uint32_t n, const tqs_gate *gates, size_t ng, Circuit &out)
+{
+    if (n < 1 || n > TQS_MAX_QUBITS)
+        return "n_qubits must be in [1, " + std::to_string(TQS_MAX_QUBITS) + "]";
+    if (ng > 0 && gates == nullptr)
+        return "gates is NULL";
+    if (ng > 60000)
+        return "at most 60000 gates are supported";
+    out.n = n;
+    out.gates.resize(ng);
+    for (size_t i = 0; i < ng; i++) {
+        const tqs_gate &g = gates[i];
+        std::string at = "gate " + std::to_string(i) + ": ";
+        if (g.kind > TQS_U2)
+            return at + "unknown kind " + std::to_string(g.kind);
+        if (g.q0 >= n)
+            return at + "q0 out of range";
+        bool two = is_two_qubit(g.kind);
+        if (two && (g.q1 >= n || g.q1 == g.q0))
+            return at + "q1 out of range or equal to q0";
+        if (!std::isfinite(g.theta))
+            return at + "non-finite angle";
+        int d = (g.kind == TQS_U1) ? 4 : (g.kind == TQS_U2 ? 16 : 0);
+        if (d && g.mat == nullptr)
+            return at + "U1/U2 need a matrix";
+        for (int j = 0; j < 2 * d; j++)
+            if (!std::isfinite(g.mat[j]))
+                return at + "non-finite matrix entry";
+        Gate &o = out.gates[i];
+        o.kind = g.kind;
+        o.q0 = g.q0;
+        o.q1 = two ? g.q1 : g.q0;
+        o.theta = g.theta;
+        gate_matrix(g.kind, g.theta, g.mat, o.m);
+    }
+    return "";
+}
+
+// --------------------------------------------------------------------------
+// Partitioners
+// --------------------------------------------------------------------------
+static std::vector<uint32_t> equal_split(uint32_t G, uint32_t L)
+{
+    std::vector<uint32_t> s(L + 1);
+    for (uint32_t i = 0; i <= L; i++)
+        s[i] = (uint32_t)(((uint64_t)i * G) / L);
+    return s;
+}
+
+// a^k * b <= N without overflow
+static bool pow_times_le(uint64_t a, uint32_t k, uint64_t b, uint64_t N)
+{
+    unsigned __int128 v = b;
+    for (uint32_t i = 0; i < k; i++) {
+        v *= a;
+        if (v > N)
+            return false;
+    }
+    return v <= N;
+}
+
+// Dynamic Circuit Partition (Sec. 3.2): the first-subcircuit error rate
+// (Eq. error_rate) sets the minimum first-level arity by the sample-size formula
+// (Eq. sample_size_formula); the remaining k levels take the equal arity
+// floor((N / A_0)^(1/k)) (Eq. subcirc_shots) with k as large as keeps it >= 2
+// and no larger than the state-copy limit (at least c gates per subcircuit,
+// Sec. 3.6); A_0 is then raised to ceil(N / A_r^k) so that the tree has N
+// leaves, and the circuit is cut into k+1 subcircuits of equal length.
+static std::string dcp(const Circuit &c, const Noise &nz, uint64_t N, double z, double eps,
+                       uint32_t cgates, std::vector<uint64_t> &arity, std::vector<uint32_t> &split)
+{
+    const uint32_t G = (uint32_t)c.gates.size();
+    std::vector<double> e(G);
+    for (uint32_t i = 0; i < G; i++)
+        e[i] = is_two_qubit(c.gates[i].kind) ? nz.p2 : nz.p1;
+    uint32_t cap = (cgates ? G / cgates : G);
+    cap = cap >= 1 ? cap - 1 : 0;
+    uint32_t K = cap;
+    uint64_t a0min = 1;
+    for (;;) {
+        uint32_t first = G ? (G + K) / (K + 1) : 0;  // ceil(G / (K+1))
+        double prod = 1.0;
+        for (uint32_t i = 0; i < first; i++)
+            prod *= (1.0 - e[i]);
+        double ph = 1.0 - prod;
+        double n0 = z * z * ph * (1.0 - ph) / (eps * eps);
+        double a = std::ceil(n0 / (1.0 + n0 / (double)N));
+        a0min = a < 1.0 ? 1 : (uint64_t)a;
+        uint32_t ks = 0;
+        while (ks < 63 && pow_times_le(2, ks + 1, a0min, N))
+            ks++;
+        uint32_t Kn = std::min(std::min(ks, cap), K);
+        if (Kn == K)
+            break;
+        K = Kn;
+    }
+    if (K == 0) {
+        arity = {N};
+        split = {0, G};
+        return "";
+    }
+    // the ABI holds at most TQS_MAX_LEVELS levels; a deeper fixed point is cut there
+    if (K > TQS_MAX_LEVELS - 1)
+        K = TQS_MAX_LEVELS - 1;
+    uint64_t ar = 2;
+    while (pow_times_le(ar + 1, K, a0min, N))
+        ar++;
+    unsigned __int128 pk = 1;
+    for (uint32_t i = 0; i < K; i++)
+        pk *= ar;
+    uint64_t a0 = (uint64_t)(((unsigned __int128)N + pk - 1) / pk);
+    arity.assign(K + 1, ar);
+    arity[0] = a0;
+    split = equal_split(G, K + 1);
+    return "";
+}
+
+std::string partition(const Circuit &c, const Noise &nz, uint64_t N, const tqs_options &o,
+                      std::vector<uint64_t> &arity, std::vector<uint32_t> &split)
+{
+    const uint32_t G = (uint32_t)c.gates.size();
+    if (N == 0)
+        return "shots must be >= 1";
+    if (o.mode == TQS_MODE_BASELINE) {
+        arity = {N};
+        split = {0, G};
+        return "";
+    }
+    if (o.mode != TQS_MODE_TREE)
+        return "unknown mode";
+    switch (o.part) {
+    case TQS_PART_DCP:
+        if (!(o.z > 0) || !(o.eps > 0) || !std::isfinite(o.z) || !std::isfinite(o.eps))
+            return "DCP needs z > 0 and eps > 0";
+        return dcp(c, nz, N, o.z, o.eps, o.copy_gates, arity, split);
+    case TQS_PART_UCP:
+    case TQS_PART_XCP: {
+        uint32_t L = o.k + 1;
+        if (L > TQS_MAX_LEVELS)
+            return "too many levels";
+        uint64_t ratio = o.part == TQS_PART_XCP ? 2 : 1;
+        for (uint64_t a = 1;; a++) {
+            unsigned __int128 prod = 1;
+            std::vector<uint64_t> ar(L);
+            for (uint32_t i = 0; i < L; i++) {
+                unsigned __int128 v = a;
+                for (uint32_t j = 0; j + 1 + i < L; j++)
+                    v *= ratio;
+                ar[i] = (uint64_t)v;
+                prod *= v;
+                if (prod > ((unsigned __int128)1 << 100))
+                    break;
+            }
+            if (prod >= N) {
+                arity = ar;
+                split = equal_split(G, L);
+                return "";
+            }
+        }
+    }
+    case TQS_PART_EXPLICIT: {
+        uint32_t L = o.k + 1;
+        if (L > TQS_MAX_LEVELS || !o.arity || !o.split)
+            return "explicit tree needs k < 17, arity and split";
+        arity.assign(o.arity, o.arity + L);
+        split.assign(o.split, o.split + L + 1);
+        unsigned __int128 prod = 1;
+        for (uint64_t a : arity) {
+            if (a == 0)
+                return "arity must be >= 1";
+            prod *= a;
+            if (prod > ((unsigned __int128)1 << 100))
+                prod = ((unsigned __int128)1 << 100);
+        }
+        if (prod < N)
+            return "prod(arity) must be >= shots";
+        if (split[0] != 0 || split[L] != G)
+            return "split must start at 0 and end at n_gates";
+        for (uint32_t i = 0; i < L; i++)
+            if (split[i + 1] < split[i])
+                return "split must be non-decreasing";
+        return "";
+    }
+    case TQS_PART_LEARNED:
+        return "UNSUPPORTED:the learned partitioner is not available in this build";
+    default:
+        return "unknown partitioner";
+    }
+}
+
+// --------------------------------------------------------------------------
+// Lowering: lazy SWAPs, noise sites, tile passes, sampler layout
+// --------------------------------------------------------------------------
+static void choose_tile(uint32_t n, uint32_t tmax, uint32_t need_mask, const uint8_t *prefer,
+                        uint32_t nprefer, Pass &p)
+{
+    uint32_t t = std::min(n, tmax);
+    uint32_t lmin = std::min<uint32_t>(n, 4);
+    uint32_t T = need_mask;
+    for (uint32_t b = 0; b < lmin; b++)
+        T |= 1u << b;
+    for (uint32_t i = 0; i < nprefer && (uint32_t)__builtin_popcount(T) < t; i++)
+        T |= 1u << prefer[i];
+    for (uint32_t b = 0; b < n && (uint32_t)__builtin_popcount(T) < t; b++)
+        T |= 1u << b;
+    p.t = (uint32_t)__builtin_popcount(T);
+    uint32_t j = 0, h = 0;
+    for (uint32_t b = 0; b < n; b++) {
+        if (T & (1u << b))
+            p.tbits[j++] = (uint8_t)b;
+        else
+            p.hbits[h++] = (uint8_t)b;
+    }
+    uint32_t L = 0;
+    while (L < p.t && p.tbits[L] == L)
+        L++;
+    p.L = L;
+}
+
+std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const tqs_options &o,
+                       const std::vector<uint64_t> &arity, const std::vector<uint32_t> &split,
+                       PlanHost &P)
+{
+    const uint32_t n = c.n, G = (uint32_t)c.gates.size();
+    const uint32_t L = (uint32_t)arity.size();
+    P = PlanHost();
+    P.n = n;
+    P.prec = o.prec;
+    P.mode = o.mode;
+    P.shots = shots;
+    uint32_t tdef = o.prec == TQS_FP64 ? 11 : 12;
+    uint32_t tmax = o.tile_qubits ? o.tile_qubits : tdef;
+    if (tmax < 6 || tmax > (uint32_t)kMaxTile)
+        return "tile_qubits must be in [6, 13]";
+    P.tile_max = tmax;
+    P.thr1 = threshold32(nz.p1);
+    P.thr2 = threshold32(nz.p2);
+    P.thrm = threshold32(nz.pm);
+
+    // lowered matrices: dense gates keep the full matrix, diagonal gates their diagonal
+    P.mats64.assign((size_t)std::max<uint32_t>(G, 1) * 32, 0.0);
+    std::vector<uint8_t> op(G);
+    for (uint32_t g = 0; g < G; g++) {
+        const Gate &gt = c.gates[g];
+        bool two = is_two_qubit(gt.kind);
+        double *dst = &P.mats64[(size_t)g * 32];
+        if (gt.kind == TQS_SWAP) {
+            op[g] = OP_NOP;
+            continue;
+        }
+        int d = two ? 4 : 2;
+        bool diag = is_diagonal(gt.kind);
+        if (gt.kind == TQS_U1 || gt.kind == TQS_U2) {
+            diag = true;
+            for (int r = 0; r < d; r++)
+                for (int k = 0; k < d; k++)
+                    if (r != k && (gt.m[2 * (r * d + k)] != 0.0 || gt.m[2 * (r * d + k) + 1] != 0.0))
+                        diag = false;
+        }
+        if (diag) {
+            op[g] = two ? OP_DIAG2 : OP_DIAG1;
+            for (int r = 0; r < d; r++) {
+                dst[2 * r] = gt.m[2 * (r * d + r)];
+                dst[2 * r + 1] = gt.m[2 * (r * d + r) + 1];
+            }
+        } else {
+            op[g] = two ? OP_DENSE2 : OP_DENSE1;
+            std::memcpy(dst, gt.m, sizeof(double) * 2 * d * d);
+        }
+    }
+    P.mats32.resize(P.mats64.size());
+    for (size_t i = 0; i < P.mats64.size(); i++)
+        P.mats32[i] = (float)P.mats64[i];
+
+    // physical qubit of every gate with SWAPs made lazy (a relabelling only)
+    std::vector<uint8_t> perm(n);
+    for (uint32_t q = 0; q < n; q++)
+        perm[q] = (uint8_t)q;
+    struct Lowered { uint8_t p0, p1, np0, np1; };
+    std::vector<Lowered> low(G);
+    std::vector<std::vector<uint8_t>> perm_after(G + 1);
+    perm_after[0] = perm;
+    for (uint32_t g = 0; g < G; g++) {
+        const Gate &gt = c.gates[g];
+        if (gt.kind == TQS_SWAP)
+            std::swap(perm[gt.q0], perm[gt.q1]);
+        low[g].p0 = perm[gt.q0];
+        low[g].p1 = perm[gt.q1];
+        low[g].np0 = perm[gt.q0];
+        low[g].np1 = perm[gt.q1];
+        perm_after[g + 1] = perm;
+    }
+
+    // levels
+    uint64_t below = 1;
+    P.levels.resize(L);
+    for (int i = (int)L - 1; i >= 0; i--) {
+        Level &lv = P.levels[i];
+        lv.g0 = split[i];
+        lv.g1 = split[i + 1];
+        lv.arity = arity[i];
+        lv.below = below;
+        unsigned __int128 act = ((unsigned __int128)shots + below - 1) / below;
+        lv.active = (uint64_t)act;
+        unsigned __int128 nb = (unsigned __int128)below * arity[i];
+        below = nb > ((unsigned __int128)1 << 63) ? ((uint64_t)1 << 63) : (uint64_t)nb;
+        lv.perm = perm_after[lv.g1];
+    }
+
+    // tile passes per level (greedy: grow the set of qubits that dense gates need
+    // until it no longer fits a tile)
+    for (uint32_t i = 0; i < L; i++) {
+        Level &lv = P.levels[i];
+        lv.pass_begin = (uint32_t)P.passes.size();
+        uint32_t g = lv.g0;
+        do {
+            uint32_t need = 0, start = g;
+            uint32_t lowbits = (1u << std::min<uint32_t>(n, 4)) - 1;
+            for (; g < lv.g1; g++) {
+                uint32_t add = 0;
+                if (op[g] == OP_DENSE1)
+                    add = 1u << low[g].p0;
+                else if (op[g] == OP_DENSE2)
+                    add = (1u << low[g].p0) | (1u << low[g].p1);
+                if ((uint32_t)__builtin_popcount(need | add | lowbits) > std::min(n, tmax))
+                    break;
+                need |= add;
+            }
+            Pass ps;
+            std::memset(&ps, 0, sizeof(ps));
+            ps.level = i;
+            ps.site_begin = start - lv.g0;
+            choose_tile(n, tmax, need, nullptr, 0, ps);
+            ps.ibeg = (uint32_t)P.instrs.size();
+            uint8_t pos[32];
+            std::memset(pos, 0xff, sizeof(pos));
+            for (uint32_t j = 0; j < ps.t; j++)
+                pos[ps.tbits[j]] = (uint8_t)j;
+            for (uint32_t k = start; k < g; k++) {
+                Instr in;
+                std::memset(&in, 0, sizeof(in));
+                in.op = op[k];
+                in.p0 = low[k].p0;
+                in.p1 = low[k].p1;
+                in.j0 = pos[low[k].p0];
+                in.j1 = pos[low[k].p1];
+                in.np0 = low[k].np0;
+                in.np1 = low[k].np1;
+                in.npaulis = is_two_qubit(c.gates[k].kind) ? 15 : 3;
+                in.site = (uint16_t)(k - lv.g0);
+                in.gate = k;
+                P.instrs.push_back(in);
+            }
+            ps.iend = (uint32_t)P.instrs.size();
+            P.passes.push_back(ps);
+        } while (g < lv.g1);
+        lv.pass_end = (uint32_t)P.passes.size();
+    }
+
+    // final pass: prefer the physical homes of the lowest logical outcome bits
+    Pass &fin = P.passes.back();
+    const std::vector<uint8_t> &pf = P.levels.back().perm;
+    {
+        uint32_t need = 0;
+        for (uint32_t k = fin.ibeg; k < fin.iend; k++) {
+            const Instr &in = P.instrs[k];
+            if (in.op == OP_DENSE1)
+                need |= 1u << in.p0;
+            else if (in.op == OP_DENSE2)
+                need |= (1u << in.p0) | (1u << in.p1);
+        }
+        choose_tile(n, tmax, need, pf.data(), std::min<uint32_t>(n, kMaxGamma), fin);
+        uint8_t pos[32];
+        std::memset(pos, 0xff, sizeof(pos));
+        for (uint32_t j = 0; j < fin.t; j++)
+            pos[fin.tbits[j]] = (uint8_t)j;
+        for (uint32_t k = fin.ibeg; k < fin.iend; k++) {
+            P.instrs[k].j0 = pos[P.instrs[k].p0];
+            P.instrs[k].j1 = pos[P.instrs[k].p1];
+        }
+    }
+
+    // sampler layout of the final pass
+    SamplerLayout &S = P.samp;
+    std::memset(&S, 0, sizeof(S));
+    uint8_t inv[32];
+    for (uint32_t q = 0; q < n; q++) {
+        S.phys_of_logical[q] = pf[q];
+        inv[pf[q]] = (uint8_t)q;
+    }
+    uint32_t qH = n;
+    for (uint32_t h = 0; h < n - fin.t; h++) {
+        S.logical_of_hbit[h] = inv[fin.hbits[h]];
+        qH = std::min<uint32_t>(qH, inv[fin.hbits[h]]);
+    }
+    S.gamma = std::min<uint32_t>(qH, kMaxGamma);
+    S.groups = (uint64_t)1 << (n - S.gamma);
+    // ranks: tile positions ordered by their logical bit
+    std::vector<std::pair<uint8_t, uint8_t>> lr;
+    for (uint32_t j = 0; j < fin.t; j++)
+        lr.push_back({inv[fin.tbits[j]], (uint8_t)j});
+    std::sort(lr.begin(), lr.end());
+    for (uint32_t q = 0; q < 32; q++)
+        S.rank_of_logical[q] = -1;
+    for (uint32_t r = 0; r < fin.t; r++) {
+        S.rank_q[r] = lr[r].first;
+        S.rank_pos[r] = lr[r].second;
+        S.rank_of_logical[lr[r].first] = (int8_t)r;
+    }
+    for (uint32_t r = 0; r < S.gamma; r++)
+        if (S.rank_q[r] != r)
+            return "internal: sampler layout invariant broken";
+    return "";
+}
+
+}  // namespace tqs
