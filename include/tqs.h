@@ -202,6 +202,31 @@ tqs_status tqs_debug_node_noise(const tqs_circuit *c, const tqs_noise *nz, uint6
                                 uint64_t seed, const tqs_options *opts, uint32_t level,
                                 uint64_t node, uint8_t *paulis_out);
 
+/* Simulation without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory, such as
+ * code that runs while another component owns the whole device through its own
+ * pool allocator, latency-critical loops where cudaMalloc/cudaFree would
+ * synchronise the device, and plugin hosts that forbid allocation.
+ *
+ * It runs the same simulation as tqs_plan_create + tqs_plan_execute, but all
+ * device scratch (gate tables, noise tables, Pauli frames, the state pool and
+ * the measurement block sums) lives in one static array of
+ * TQS_STATIC_SCRATCH_BYTES bytes inside the library, which every GPU that loads
+ * the library keeps reserved until the process exits.  The node batch shrinks to
+ * fit the array; a request that does not fit with one node per level returns
+ * TQS_EINVAL and says how many bytes it needs.  opts->workspace, workspace_bytes
+ * and TQS_FLAG_PROFILE are ignored.
+ *
+ * d_counts: caller-owned DEVICE array of 2^n uint64, zeroed by the call, then
+ * the histogram (sums to shots).  The call runs on opts->stream and returns
+ * after the simulation has finished.  The first call on each device (with that
+ * device current) looks up the array's device address once; make that first
+ * call before any stream capture.  Every call shares the one array: calls whose
+ * GPU work overlaps (different streams or threads) race on it, so serialise them. */
+#define TQS_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+tqs_status tqs_simulate_static(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, uint64_t seed,
+                               const tqs_options *opts, uint64_t *d_counts);
+
 const char *tqs_last_error(void);
 int tqs_abi_version(void);
 

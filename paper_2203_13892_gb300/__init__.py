@@ -25,4 +25,5 @@ from .capi import (  # noqa: F401
     tqs_plan_execute,
     tqs_plan_workspace_bytes,
     tqs_simulate,
+    tqs_simulate_static,
 )

@@ -84,8 +84,10 @@ EXPORTS = (
     "tqs_circuit_create", "tqs_circuit_destroy", "tqs_noise_model", "tqs_noise_destroy",
     "tqs_options_default", "tqs_partition", "tqs_simulate", "tqs_plan_create",
     "tqs_plan_execute", "tqs_plan_workspace_bytes", "tqs_plan_destroy",
-    "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_last_error", "tqs_abi_version",
+    "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_simulate_static", "tqs_last_error",
+    "tqs_abi_version",
 )
+TQS_STATIC_SCRATCH_BYTES = 32 << 20
 
 
 def lib():
@@ -124,6 +126,8 @@ def lib():
             L.tqs_debug_node_noise.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.POINTER(tqs_options),
                                                C.c_uint32, C.c_uint64, C.POINTER(C.c_uint8)]
             L.tqs_debug_node_noise.restype = st
+            L.tqs_simulate_static.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.POINTER(tqs_options), vp]
+            L.tqs_simulate_static.restype = st
             L.tqs_last_error.restype = C.c_char_p
             L.tqs_abi_version.restype = C.c_int
             _lib = L
@@ -293,3 +297,11 @@ def tqs_debug_node_noise(c: Handle, nz: Handle, shots: int, seed: int, opts: Opt
     _check(lib().tqs_debug_node_noise(c.ptr, nz.ptr, int(shots), int(seed), C.byref(opts) if opts else None,
                                       int(level), int(node), out.ctypes.data_as(C.POINTER(C.c_uint8))))
     return out[:sites]
+
+
+def tqs_simulate_static(c: Handle, nz: Handle, shots: int, seed: int, opts: Optional[tqs_options],
+                        d_counts: int) -> None:
+    """Simulation whose device scratch is the library's static array (no device
+    allocation); d_counts is the device address of a 2^n uint64 histogram."""
+    _check(lib().tqs_simulate_static(c.ptr, nz.ptr, int(shots), int(seed), C.byref(opts) if opts else None,
+                                     C.c_void_p(int(d_counts))))

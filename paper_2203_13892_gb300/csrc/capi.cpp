@@ -9,13 +9,8 @@
 #include <string>
 
 #include "executor.h"
+#include "handles.h"
 
-struct tqs_circuit {
-    tqs::Circuit c;
-};
-struct tqs_noise {
-    tqs::Noise nz;
-};
 struct tqs_plan {
     tqs::Circuit c;
     tqs::Noise nz;
@@ -150,6 +145,8 @@ tqs_status fidelity(const tqs_circuit *c, uint64_t shots, const unsigned long lo
     return TQS_OK;
 }
 }  // namespace
+
+tqs_status tqs::set_error(tqs_status s, const std::string &msg) { return fail(s, msg); }
 
 extern "C" {
 
