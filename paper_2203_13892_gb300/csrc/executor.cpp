@@ -97,6 +97,8 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
     size_t o_instr = take(sizeof(Instr) * std::max<size_t>(H.instrs.size(), 1));
     size_t o_mats = take((H.prec == TQS_FP64 ? 8 : 4) * H.mats64.size());
     size_t o_pst = take(sizeof(uint32_t) * (H.passes.size() + L) + 64);
+    size_t o_prog = take(std::max<size_t>(H.prog.size(), 16));
+    size_t o_choff = take(sizeof(uint32_t) * std::max<size_t>(H.chunk_off.size(), 1));
     size_t o_fid = take(sizeof(double) * (3 + 3 * 256));
     size_t o_perm = take(32);
     size_t o_counts = take(sizeof(uint64_t) * ((size_t)1 << H.n));
@@ -116,6 +118,8 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
         d_instr = (Instr *)(b + o_instr);
         d_mats = b + o_mats;
         d_pass_start = (uint32_t *)(b + o_pst);
+        d_prog = (uint8_t *)(b + o_prog);
+        d_chunk_off = (uint32_t *)(b + o_choff);
         d_fid = (double *)(b + o_fid);
         d_perm = (uint8_t *)(b + o_perm);
         d_counts_internal = (unsigned long long *)(b + o_counts);
@@ -191,6 +195,9 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
         pst_host.push_back(lv.g1 - lv.g0);
     }
     CK(cudaMemcpyAsync(d_pass_start, pst_host.data(), 4 * pst_host.size(), cudaMemcpyHostToDevice, stream));
+    if (!H.prog.empty())
+        CK(cudaMemcpyAsync(d_prog, H.prog.data(), H.prog.size(), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_chunk_off, H.chunk_off.data(), 4 * H.chunk_off.size(), cudaMemcpyHostToDevice, stream));
     uint8_t perm[32] = {0};
     for (uint32_t q = 0; q < H.n; q++)
         perm[q] = H.levels.back().perm[q];
@@ -247,6 +254,10 @@ tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vect
         a.instr = d_instr;
         a.ibeg = ps.ibeg;
         a.iend = ps.iend;
+        a.prog = d_prog;
+        a.chunk_off = d_chunk_off;
+        a.chunk_begin = ps.chunk_begin;
+        a.chunk_end = ps.chunk_end;
         a.n = H.n;
         a.t = ps.t;
         a.L = ps.L;
@@ -368,6 +379,10 @@ tqs_status DevicePlan::run_chain(uint32_t level, uint64_t node, uint64_t seed, s
             a.instr = d_instr;
             a.ibeg = ps.ibeg;
             a.iend = ps.iend;
+            a.prog = d_prog;
+            a.chunk_off = d_chunk_off;
+            a.chunk_begin = ps.chunk_begin;
+            a.chunk_end = ps.chunk_end;
             a.n = H.n;
             a.t = ps.t;
             a.L = ps.L;

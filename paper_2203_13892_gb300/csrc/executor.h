@@ -24,6 +24,8 @@ struct DevicePlan {
     Instr *d_instr = nullptr;
     void *d_mats = nullptr;
     uint32_t *d_pass_start = nullptr;
+    uint8_t *d_prog = nullptr;
+    uint32_t *d_chunk_off = nullptr;
     double *d_fid = nullptr;
     uint8_t *d_perm = nullptr;
     unsigned long long *d_counts_internal = nullptr;

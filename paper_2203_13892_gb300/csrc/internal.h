@@ -14,6 +14,8 @@ namespace tqs {
 constexpr int kThreads = 256;      // threads per CTA of every state kernel
 constexpr int kMaxTile = 13;       // largest shared-memory tile (2^13 amplitudes)
 constexpr int kMaxGamma = 8;       // sampler group = up to 2^8 consecutive outcomes
+constexpr int kProgChunkBytes = 6144;  // pass-program bytes staged in shared memory at a time
+constexpr int kNoiseStage = 4096;      // noise bytes of a node staged in shared memory
 constexpr uint32_t kDomNoise = 1, kDomMeas = 2, kDomRead = 3;
 
 // ---------------------------------------------------------------------------
@@ -29,7 +31,7 @@ struct Instr {
     uint8_t np0, np1;    // physical bits of the noise site's qubits (a on np0, b on np1)
     uint8_t npaulis;     // 3 (one-qubit site) or 15 (two-qubit site)
     uint16_t site;       // site index relative to the level's first gate
-    uint16_t pad;
+    uint16_t pad;        // diagonal ops: bit k set iff factor k (G, a0, a1, c) != 1
     uint32_t gate;       // global gate index (row of the matrix tables)
 };
 static_assert(sizeof(Instr) == 16, "Instr layout");
@@ -59,9 +61,43 @@ struct Noise {
     double p1, p2, pm;
 };
 
+// Compiled pass program: 16-byte aligned records walked in order by every
+// thread of a CTA (uniform).  Record header, then a payload of complex values
+// in the state's precision (R = float or double, C = complex of R):
+//   REC_DENSE1  a=j b=p                 payload U[2x2]             noise site `site`
+//   REC_DENSE2  a=j0 b=j1 c=p0 d=p1     payload U[4x4]             noise site `site`
+//   REC_RUN     a..e = factor counts    payload G, then factors    sites [ibeg, iend) of the
+//               of kinds A_FIXED, A_SLOT, C_FIXED, C_MIXED, C_SLOTS (in that order) for the
+//               run of consecutive diagonal gates (and lazy SWAPs) it aggregates
+// DENSE1 sets c = 1 when the matrix is real.  A factor record is an 8-byte FacHdr
+// followed by its complex value at the next multiple of sizeof(C) (16 or 32 bytes).
+// A run's factors: the product over its gates of D = G * prod a_q^{x_q} *
+// prod c_qr^{x_q x_r}, merged per qubit and per pair and classified by where
+// the bits live (thread bit, register slot bit, outside the tile).
+enum RecType : uint8_t { REC_DENSE1 = 1, REC_DENSE2 = 2, REC_RUN = 3 };
+enum FacKind : uint8_t {
+    FAC_A_FIXED = 1,   // a^{x_p}, p a thread bit or outside the tile
+    FAC_A_SLOT = 2,    // a^{x}, on slot bit s = j0 - 8
+    FAC_C_FIXED = 4,   // c^{x_p0 x_p1}, neither on a slot bit
+    FAC_C_MIXED = 5,   // c^{x_p0 x_s1}, p0 fixed, s1 = j1 - 8 a slot bit
+    FAC_C_SLOTS = 7    // c^{x_s0 x_s1}, both slot bits
+};
+struct RecHdr {
+    uint8_t type, a, b, c;
+    uint8_t d, e;
+    uint16_t site;        // noise site (dense) / first site (run), level-relative
+    uint32_t ibeg, iend;  // instruction range (the run's gates, for the per-gate fallback)
+};
+static_assert(sizeof(RecHdr) == 16, "RecHdr layout");
+struct FacHdr {
+    uint8_t kind, j0, p0, j1, p1, pad0, pad1, pad2;
+};
+static_assert(sizeof(FacHdr) == 8, "FacHdr layout");
+
 struct Pass {
     uint32_t level;
     uint32_t ibeg, iend;          // instruction range (global instruction list)
+    uint32_t chunk_begin, chunk_end;  // program chunks (offsets in PlanHost::chunk_off)
     uint32_t site_begin;          // first site of the pass, relative to the level
     uint32_t t, L;                // tile width and number of contiguous low bits
     uint8_t tbits[kMaxTile];      // physical bit of each tile position (ascending)
@@ -99,6 +135,8 @@ struct PlanHost {
     std::vector<Instr> instrs;
     std::vector<double> mats64;    // 32 doubles per gate
     std::vector<float> mats32;     // 32 floats per gate
+    std::vector<uint8_t> prog;     // compiled pass programs (state precision), all passes
+    std::vector<uint32_t> chunk_off; // chunk boundaries into prog (chunk c = [off[c], off[c+1]))
     uint64_t thr1, thr2, thrm;     // floor(p * 2^32)
     SamplerLayout samp;
     uint32_t tile_max;
@@ -154,6 +192,9 @@ struct PassLaunch {
     uint32_t nnodes;
     const Instr *instr;
     uint32_t ibeg, iend;
+    const uint8_t *prog;
+    const uint32_t *chunk_off;
+    uint32_t chunk_begin, chunk_end;
     uint32_t n, t, L;
     uint8_t tbits[kMaxTile];
     uint8_t hbits[32];

@@ -152,6 +152,8 @@ struct PassK {
     uint64_t state_elems;
     uint64_t node_lo, parent_lo, arity;
     const Instr *instr;
+    const uint8_t *prog;
+    const uint32_t *chunk_off;
     const void *mats;
     const uint8_t *noise;
     const NodeMeta *meta;
@@ -159,6 +161,7 @@ struct PassK {
     unsigned long long *counts;
     uint64_t seed, thrm;
     uint32_t ibeg, iend, n, t, L, sites, meta_stride, pass_local;
+    uint32_t chunk_begin, chunk_end;
     int in_from_parent;
     uint8_t tbits[kMaxTile];
     uint8_t hbits[32];
@@ -213,7 +216,7 @@ __device__ uint64_t block_pick(uint64_t count, double target, F val, double *res
     for (uint64_t i = b; i < e; i++) {
         const double v = val(i);
         local += v;
-        if (v > 0.0)
+        if (__double_as_longlong(v) != 0)  // values are >= 0: nonzero iff any bit set
             lastnz = i;
     }
     if (threadIdx.x == 0) {
@@ -266,41 +269,243 @@ __device__ uint64_t block_pick(uint64_t count, double target, F val, double *res
     return pick;
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(kThreads) pass_kernel(const __grid_constant__ PassK a)
+// Per-thread accumulator of a run of diagonal factors (Pauli Z signs included).
+// A diagonal block is D(x) = prod_g G_g * prod_q a_q^{x_q} * prod_{q<r} c_qr^{x_q x_r}
+// over logical bits x.  The thread knows its own bits on thread positions and
+// the CTA's bits outside the tile, so those factors collapse into `base`; a
+// factor on a slot bit s (register index bit) goes to E[s]; slot-slot pairs go to
+// Gs.  Applying the block costs one complex product per amplitude.
+template <typename C, int NS> struct DiagAcc {
+    C base;
+    C E[NS > 0 ? NS : 1];
+    C Gs[NS > 1 ? NS * (NS - 1) / 2 : 1];
+    bool has_gs;
+    __device__ __forceinline__ void reset()
+    {
+        base = mk((decltype(base.x))1, (decltype(base.x))0);
+#pragma unroll
+        for (int s = 0; s < NS; s++)
+            E[s] = base;
+#pragma unroll
+        for (int i = 0; i < (NS > 1 ? NS * (NS - 1) / 2 : 1); i++)
+            Gs[i] = base;
+        has_gs = false;
+    }
+    __device__ __forceinline__ void mul_E(int s, C f)
+    {
+        // s is uniform across the CTA: a branch, not predicated copies
+        switch (s) {
+        case 0: if (NS > 0) E[0] = cmul(E[0], f); break;
+        case 1: if (NS > 1) E[NS > 1 ? 1 : 0] = cmul(E[NS > 1 ? 1 : 0], f); break;
+        case 2: if (NS > 2) E[NS > 2 ? 2 : 0] = cmul(E[NS > 2 ? 2 : 0], f); break;
+        case 3: if (NS > 3) E[NS > 3 ? 3 : 0] = cmul(E[NS > 3 ? 3 : 0], f); break;
+        default: if (NS > 4) E[NS > 4 ? 4 : 0] = cmul(E[NS > 4 ? 4 : 0], f); break;
+        }
+    }
+    __device__ __forceinline__ void mul_Gs(int s0, int s1, C f)
+    {
+        const int hi = s0 > s1 ? s0 : s1, lo = s0 > s1 ? s1 : s0;
+        const int idx = hi * (hi - 1) / 2 + lo;
+#pragma unroll
+        for (int k = 0; k < (NS > 1 ? NS * (NS - 1) / 2 : 1); k++)
+            if (k == idx)
+                Gs[k] = cmul(Gs[k], f);
+        has_gs = true;
+    }
+};
+
+// tile position j: thread bit (j < 8 or tile smaller than the CTA), slot bit s = j-8, or outside (0xff)
+__device__ __forceinline__ bool thread_or_outside(uint32_t j) { return j == 0xffu || j < 8u; }
+
+template <typename C, int NS>
+__device__ __forceinline__ void acc_alpha(DiagAcc<C, NS> &A, uint32_t j, uint32_t p, uint32_t xt, C f)
+{
+    if (thread_or_outside(j)) {
+        if ((xt >> p) & 1u)
+            A.base = cmul(A.base, f);
+    } else {
+        A.mul_E((int)j - 8, f);
+    }
+}
+
+template <typename C, int NS>
+__device__ __forceinline__ void acc_gamma(DiagAcc<C, NS> &A, uint32_t j0, uint32_t p0, uint32_t j1, uint32_t p1,
+                                          uint32_t xt, C f)
+{
+    const bool a = thread_or_outside(j0), b = thread_or_outside(j1);
+    if (a && b) {
+        if ((xt >> p0) & (xt >> p1) & 1u)
+            A.base = cmul(A.base, f);
+    } else if (a) {
+        if ((xt >> p0) & 1u)
+            A.mul_E((int)j1 - 8, f);
+    } else if (b) {
+        if ((xt >> p1) & 1u)
+            A.mul_E((int)j0 - 8, f);
+    } else {
+        A.mul_Gs((int)j0 - 8, (int)j1 - 8, f);
+    }
+}
+
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+
+// Multiply the NR register amplitudes by the accumulated diagonal.  msig: the
+// frame mask restricted to the slot bits (bit s = mask bit of slot position s).
+template <typename C, int LOGR>
+__device__ __forceinline__ void acc_flush(DiagAcc<C, LOGR> &A, C (&v)[1 << LOGR], uint32_t msig)
+{
+    constexpr int NR = 1 << LOGR;
+    // rewrite the slot factors from logical bits x_s = b_s ^ m_s to register bits b_s
+    C Eb[LOGR > 0 ? LOGR : 1];
+    C base = A.base;
+#pragma unroll
+    for (int s = 0; s < LOGR; s++) {
+        if ((msig >> s) & 1u) {
+            base = cmul(base, A.E[s]);
+            Eb[s] = cconj(A.E[s]);
+        } else {
+            Eb[s] = A.E[s];
+        }
+    }
+    C Gb[LOGR > 1 ? LOGR * (LOGR - 1) / 2 : 1];
+    if (A.has_gs) {
+#pragma unroll
+        for (int hi = 1; hi < LOGR; hi++)
+#pragma unroll
+            for (int lo = 0; lo < hi; lo++) {
+                const int idx = hi * (hi - 1) / 2 + lo;
+                const C g = A.Gs[idx];
+                const uint32_t mh = (msig >> hi) & 1u, ml = (msig >> lo) & 1u;
+                if (!mh && !ml) {
+                    Gb[idx] = g;
+                } else if (mh && !ml) {
+                    Eb[lo] = cmul(Eb[lo], g);
+                    Gb[idx] = cconj(g);
+                } else if (!mh && ml) {
+                    Eb[hi] = cmul(Eb[hi], g);
+                    Gb[idx] = cconj(g);
+                } else {
+                    base = cmul(base, g);
+                    Eb[lo] = cmul(Eb[lo], cconj(g));
+                    Eb[hi] = cmul(Eb[hi], cconj(g));
+                    Gb[idx] = g;
+                }
+            }
+    }
+    // v[k] *= base * prod_{s in k} Eb[s] * prod_{s<s' in k} Gb: one pass per factor
+#pragma unroll
+    for (int k = 0; k < NR; k++)
+        v[k] = cmul(v[k], base);
+#pragma unroll
+    for (int sb = 0; sb < LOGR; sb++)
+#pragma unroll
+        for (int k = 0; k < NR; k++)
+            if ((k >> sb) & 1)
+                v[k] = cmul(v[k], Eb[sb]);
+    if (A.has_gs) {
+#pragma unroll
+        for (int hi = 1; hi < LOGR; hi++)
+#pragma unroll
+            for (int lo = 0; lo < hi; lo++)
+#pragma unroll
+                for (int k = 0; k < NR; k++)
+                    if (((k >> hi) & 1) && ((k >> lo) & 1))
+                        v[k] = cmul(v[k], Gb[hi * (hi - 1) / 2 + lo]);
+    }
+    A.reset();
+}
+
+// Two-by-two butterfly on register bit r (pairs of slots k, k | 2^r).
+template <typename C, int LOGR>
+__device__ __forceinline__ void reg_butterfly(C (&v)[1 << LOGR], int r, C u00, C u01, C u10, C u11)
+{
+#pragma unroll
+    for (int rr = 0; rr < LOGR; rr++) {
+        if (rr == r) {
+#pragma unroll
+            for (int k = 0; k < (1 << LOGR); k++) {
+                if (!((k >> rr) & 1)) {
+                    const int k1 = k | (1 << rr);
+                    const C x0 = v[k], x1 = v[k1];
+                    v[k] = cmadd(u01, x1, cmul(u00, x0));
+                    v[k1] = cmadd(u11, x1, cmul(u10, x0));
+                }
+            }
+        }
+    }
+}
+
+template <typename C, typename R, int LOGR>
+__device__ __forceinline__ void reg_butterfly_real(C (&v)[1 << LOGR], int r, R u00, R u01, R u10, R u11)
+{
+#pragma unroll
+    for (int rr = 0; rr < LOGR; rr++) {
+        if (rr == r) {
+#pragma unroll
+            for (int k = 0; k < (1 << LOGR); k++) {
+                if (!((k >> rr) & 1)) {
+                    const int k1 = k | (1 << rr);
+                    const C x0 = v[k], x1 = v[k1];
+                    v[k] = mk(u00 * x0.x + u01 * x1.x, u00 * x0.y + u01 * x1.y);
+                    v[k1] = mk(u10 * x0.x + u11 * x1.x, u10 * x0.y + u11 * x1.y);
+                }
+            }
+        }
+    }
+}
+
+template <typename C> __device__ __forceinline__ C shfl_xor_c(C a, int m)
+{
+    return mk(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
+}
+
+#ifndef TQS_FP32_MIN_CTAS
+#define TQS_FP32_MIN_CTAS 2  // resident CTAs per SM asked of ptxas for FP32 tiles of 2^12 amplitudes
+#endif
+template <typename R, int MODE, int LOGR>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP32_MIN_CTAS : (LOGR == 3 ? 3 : 4))
+                                                           : (LOGR >= 3 ? 1 : 2))
+    pass_kernel(const __grid_constant__ PassK a)
 {
     using C = typename CT<R>::T;
+    constexpr int NR = 1 << LOGR;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t TE = 1u << a.t;
-    const uint32_t nhi = a.t - a.L;
     C *s = reinterpret_cast<C *>(smem);
-    uint32_t *dep = reinterpret_cast<uint32_t *>(s + TE);
-    uint16_t *lut = reinterpret_cast<uint16_t *>(dep + ((1u << nhi) < 4u ? 4u : (1u << nhi)));  // 256 entries
-    double *red = reinterpret_cast<double *>(lut + 256);                   // kThreads doubles
-    unsigned long long *shu = reinterpret_cast<unsigned long long *>(red + kThreads);  // 4
-    const int tid = threadIdx.x;
-    const uint32_t lomask = (1u << a.L) - 1u;
+    uint16_t *lut = reinterpret_cast<uint16_t *>(s + (TE < (uint32_t)kThreads ? (uint32_t)kThreads : TE));
+    double *red = reinterpret_cast<double *>(lut + 256);
+    unsigned long long *shu = reinterpret_cast<unsigned long long *>(red + kThreads);
+    const uint32_t tid = threadIdx.x;
+    const bool active = tid < TE;
 
     const uint32_t slot = (MODE == MODE_SAMPLE) ? blockIdx.x : blockIdx.y;
     const uint64_t node = a.node_lo + slot;
     const NodeMeta m0 = a.meta[(uint64_t)slot * a.meta_stride + a.pass_local];
     const NodeMeta m1 = a.meta[(uint64_t)slot * a.meta_stride + a.pass_local + 1];
 
-    for (uint32_t i = tid; i < (1u << nhi); i += kThreads) {
-        uint32_t d = 0;
-        for (uint32_t b = 0; b < nhi; b++)
-            if ((i >> b) & 1u)
-                d |= 1u << a.tbits[a.L + b];
-        dep[i] = d;
+    // physical offsets: thread bits (tile positions 0..7) and slot bits (8..t-1)
+    uint32_t tphys = 0;
+    const uint32_t tb = a.t < 8u ? a.t : 8u;
+    for (uint32_t j = 0; j < tb; j++)
+        tphys |= ((tid >> j) & 1u) << a.tbits[j];
+    // physical offsets of the register slots (uniform), kept in shared memory
+    uint32_t *soff = reinterpret_cast<uint32_t *>(shu + 4);
+    if (tid < (uint32_t)NR) {
+        uint32_t o = 0;
+        for (int b = 0; b < LOGR; b++)
+            if ((tid >> b) & 1u)
+                o |= 1u << a.tbits[8 + b];
+        soff[tid] = o;
     }
+
     const SamplerLayout &SL = a.samp;
     if (MODE != MODE_STORE) {
         // unkey tables: rank bits 0..6 -> tile positions (lut[0..127]), 7..13 -> lut[128..255]
         for (uint32_t i = tid; i < 256; i += kThreads) {
-            const uint32_t rb = i < 128 ? 0 : 7, v = i & 127;
+            const uint32_t rb = i < 128 ? 0 : 7, vv = i & 127;
             uint32_t e = 0;
             for (uint32_t b = 0; b < 7 && rb + b < a.t; b++)
-                if ((v >> b) & 1u)
+                if ((vv >> b) & 1u)
                     e |= 1u << SL.rank_pos[rb + b];
             lut[i] = (uint16_t)e;
         }
@@ -316,18 +521,17 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const __grid_constant__ 
             if ((h >> b) & 1u)
                 base |= 1u << a.hbits[b];
     } else {
-        // stage 1: outcome block from the block sums of this leaf
+        // stage 1: the block of 2^gamma outcomes, from this leaf's block sums
         const double *Sl = a.S + (uint64_t)slot * SL.groups;
         const uint4 r = draw(a.seed, node, 0u, kDomMeas);
         const double u = ((double)(r.x >> 5) * 67108864.0 + (double)(r.y >> 6)) * (1.0 / 9007199254740992.0);
-        // total (same chunked order as the pick)
         const uint64_t chunk = (SL.groups + kThreads - 1) / kThreads;
         double local = 0.0;
         for (uint64_t i = (uint64_t)tid * chunk; i < SL.groups && i < (uint64_t)(tid + 1) * chunk; i++)
             local += Sl[i];
         const double tot = block_incl_scan(local, red);
         if (tid == kThreads - 1)
-            red[kThreads / 32] = tot;  // slot after the warp sums
+            red[kThreads / 32] = tot;
         __syncthreads();
         const double total = red[kThreads / 32];
         __syncthreads();
@@ -347,189 +551,368 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const __grid_constant__ 
     const uint64_t in_slot = a.in_from_parent ? (node / a.arity - a.parent_lo) : slot;
     const bool synth = a.in == nullptr;
     const bool zero_tile = synth && base != 0;
+    C v[NR];
     {
         const C *src = synth ? nullptr : reinterpret_cast<const C *>(a.in) + in_slot * a.state_elems;
-        for (uint32_t e = tid; e < TE; e += kThreads) {
-            const uint32_t ph = base | dep[e >> a.L] | (e & lomask);
-            C v;
-            if (synth)
-                v = mk((R)(ph == 0 ? 1 : 0), (R)0);
+        const uint32_t tb0 = base | tphys;
+#pragma unroll
+        for (int k = 0; k < NR; k++) {
+            const uint32_t ph = tb0 | soff[k];
+            if (!active)
+                v[k] = mk((R)0, (R)0);
+            else if (synth)
+                v[k] = mk((R)(ph == 0 ? 1 : 0), (R)0);
             else
-                v = src[ph];
-            s[e] = v;
+                v[k] = src[ph];
         }
     }
 
     // ---- gates and noise -----------------------------------------------
     uint32_t mask = m0.mask;
+    uint32_t xt = (base | tphys) ^ mask;  // logical bits at thread and outside-tile positions
     const R *mats = reinterpret_cast<const R *>(a.mats);
-    const uint8_t *nz = a.noise + (uint64_t)slot * a.sites;
-    bool last_dense = true;  // the load wrote with element ownership; dense ops re-pair
-    if (!zero_tile) {
-        for (uint32_t ii = a.ibeg; ii < a.iend; ii++) {
-            const Instr I = a.instr[ii];
-            const R *M = mats + (size_t)I.gate * 32;
-            if (I.op == OP_DENSE1) {
-                __syncthreads();
-                const uint32_t mu = (mask >> I.p0) & 1u;
-                const C u00 = mk(M[2 * (0 ^ (mu * 3))], M[2 * (0 ^ (mu * 3)) + 1]);
-                const C u01 = mk(M[2 * (1 ^ (mu * 3))], M[2 * (1 ^ (mu * 3)) + 1]);
-                const C u10 = mk(M[2 * (2 ^ (mu * 3))], M[2 * (2 ^ (mu * 3)) + 1]);
-                const C u11 = mk(M[2 * (3 ^ (mu * 3))], M[2 * (3 ^ (mu * 3)) + 1]);
-                const uint32_t j = I.j0, lm = (1u << j) - 1u;
-                for (uint32_t pi = tid; pi < TE / 2; pi += kThreads) {
-                    const uint32_t e0 = ((pi & ~lm) << 1) | (pi & lm), e1 = e0 | (1u << j);
-                    const C x0 = s[e0], x1 = s[e1];
-                    s[e0] = cmadd(u01, x1, cmul(u00, x0));
-                    s[e1] = cmadd(u11, x1, cmul(u10, x0));
-                }
-                last_dense = true;
-            } else if (I.op == OP_DENSE2) {
-                __syncthreads();
-                const uint32_t mu = ((mask >> I.p0) & 1u) | (((mask >> I.p1) & 1u) << 1);
-                C u[16];
+    const uint8_t *nzg = a.noise + (uint64_t)slot * a.sites;
+    uint8_t *nzs = reinterpret_cast<uint8_t *>(soff + 32);
+    const bool nz_staged = a.sites <= (uint32_t)kNoiseStage;
+    uint8_t *pbuf = nzs + ((a.sites < (uint32_t)kNoiseStage ? a.sites : (uint32_t)kNoiseStage) + 15u) / 16u * 16u;
+    if (nz_staged)
+        for (uint32_t x = tid; x < a.sites; x += kThreads)
+            nzs[x] = nzg[x];
+    auto noise_at = [&](uint32_t site) -> uint32_t { return nz_staged ? nzs[site] : nzg[site]; };
+    DiagAcc<C, LOGR> acc;
+    acc.reset();
+    bool pending = false;
+    auto slot_mask = [&]() {
+        uint32_t m = 0;
 #pragma unroll
-                for (int r = 0; r < 4; r++)
+        for (int b = 0; b < LOGR; b++)
+            m |= ((mask >> a.tbits[8 + b]) & 1u) << b;
+        return m;
+    };
+    auto flush = [&]() {
+        if (pending) {
+            acc_flush<C, LOGR>(acc, v, slot_mask());
+            pending = false;
+        }
+    };
+    // the Pauli drawn at a noise site: Z parts join the diagonal run, X parts
+    // toggle the frame (after applying what is pending)
+    auto apply_noise = [&](uint32_t pz, uint32_t npaulis, uint32_t j0, uint32_t p0, uint32_t j1, uint32_t p1) {
+        const uint32_t wa = npaulis == 15 ? (pz >> 2) : pz;
+        const uint32_t wb = npaulis == 15 ? (pz & 3u) : 0u;
+        const C minus = mk((R)-1, (R)0);
+        if (wa >= 2) {
+            acc_alpha(acc, j0, p0, xt, minus);
+            pending = true;
+        }
+        if (wb >= 2) {
+            acc_alpha(acc, j1, p1, xt, minus);
+            pending = true;
+        }
+        const uint32_t xm = ((wa == 1 || wa == 2) ? (1u << p0) : 0u) | ((wb == 1 || wb == 2) ? (1u << p1) : 0u);
+        if (xm) {
+            flush();
+            mask ^= xm;
+            xt ^= xm;
+        }
+    };
+    auto dense1 = [&](uint32_t j, uint32_t p, C u00, C u01, C u10, C u11) {
+        flush();
+        if ((mask >> p) & 1u) {  // frame conjugation U'[r][c] = U[r^1][c^1]
+            const C t0 = u00, t1 = u01;
+            u00 = u11;
+            u01 = u10;
+            u10 = t1;
+            u11 = t0;
+        }
+        if (j >= 8) {
+            reg_butterfly<C, LOGR>(v, (int)j - 8, u00, u01, u10, u11);
+        } else if (j < 5) {
+            const uint32_t b = (tid >> j) & 1u;
+            const C cs = b ? u11 : u00, co = b ? u10 : u01;
 #pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        const int k = ((r ^ mu) * 4 + (c ^ mu));
-                        u[r * 4 + c] = mk(M[2 * k], M[2 * k + 1]);
-                    }
-                const uint32_t ja = I.j0 < I.j1 ? I.j0 : I.j1, jb = I.j0 < I.j1 ? I.j1 : I.j0;
-                const uint32_t la = (1u << ja) - 1u, lb = (1u << jb) - 1u;
-                for (uint32_t qi = tid; qi < TE / 4; qi += kThreads) {
-                    uint32_t e = ((qi & ~la) << 1) | (qi & la);
-                    e = ((e & ~lb) << 1) | (e & lb);
-                    uint32_t idx[4];
-                    C x[4];
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        idx[k] = e | ((k & 1) ? (1u << I.j0) : 0u) | ((k & 2) ? (1u << I.j1) : 0u);
-                        x[k] = s[idx[k]];
-                    }
-#pragma unroll
-                    for (int r = 0; r < 4; r++) {
-                        C acc = cmul(u[r * 4], x[0]);
-#pragma unroll
-                        for (int c = 1; c < 4; c++)
-                            acc = cmadd(u[r * 4 + c], x[c], acc);
-                        s[idx[r]] = acc;
-                    }
-                }
-                last_dense = true;
-            } else if (I.op == OP_DIAG1 || I.op == OP_DIAG2) {
-                if (last_dense)
-                    __syncthreads();
-                const C d0 = mk(M[0], M[1]), d1 = mk(M[2], M[3]);
-                C d2 = d0, d3 = d1;
-                if (I.op == OP_DIAG2) {
-                    d2 = mk(M[4], M[5]);
-                    d3 = mk(M[6], M[7]);
-                }
-                const uint32_t p1 = I.op == OP_DIAG2 ? I.p1 : I.p0;
-                for (uint32_t e = tid; e < TE; e += kThreads) {
-                    const uint32_t x = (base | dep[e >> a.L] | (e & lomask)) ^ mask;
-                    const uint32_t k = ((x >> I.p0) & 1u) | (I.op == OP_DIAG2 ? (((x >> p1) & 1u) << 1) : 0u);
-                    const C d = k == 0 ? d0 : (k == 1 ? d1 : (k == 2 ? d2 : d3));
-                    s[e] = cmul(s[e], d);
-                }
-                last_dense = false;
+            for (int k = 0; k < NR; k++) {
+                const C o = shfl_xor_c(v[k], 1 << j);
+                v[k] = cmadd(co, o, cmul(cs, v[k]));
             }
-            // the noise site after this gate
-            const uint32_t pz = nz[I.site];
-            if (pz) {
-                const uint32_t wa = I.npaulis == 15 ? (pz >> 2) : pz;
-                const uint32_t wb = I.npaulis == 15 ? (pz & 3u) : 0u;
-                const uint32_t zmask = ((wa >= 2) ? (1u << I.np0) : 0u) | ((wb >= 2) ? (1u << I.np1) : 0u);
-                if (zmask) {
-                    if (last_dense)
-                        __syncthreads();
-                    for (uint32_t e = tid; e < TE; e += kThreads) {
-                        const uint32_t x = (base | dep[e >> a.L] | (e & lomask)) ^ mask;
-                        if (__popc(x & zmask) & 1)
-                            s[e] = cneg(s[e]);
-                    }
-                    last_dense = false;
+        } else {
+            const uint32_t b = (tid >> j) & 1u;
+            const C cs = b ? u11 : u00, co = b ? u10 : u01;
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < NR; k++)
+                    s[tid + k * kThreads] = v[k];
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < NR; k++) {
+                    const C o = s[(tid ^ (1u << j)) + k * kThreads];
+                    v[k] = cmadd(co, o, cmul(cs, v[k]));
                 }
-                if (wa == 1 || wa == 2) mask ^= 1u << I.np0;
-                if (wb == 1 || wb == 2) mask ^= 1u << I.np1;
             }
         }
+    };
+    // real 2x2 matrix (H, RY, X, ...): half the multiplies
+    auto dense1_real = [&](uint32_t j, uint32_t p, R u00, R u01, R u10, R u11) {
+        flush();
+        if ((mask >> p) & 1u) {
+            const R t0 = u00, t1 = u01;
+            u00 = u11;
+            u01 = u10;
+            u10 = t1;
+            u11 = t0;
+        }
+        if (j >= 8) {
+            reg_butterfly_real<C, R, LOGR>(v, (int)j - 8, u00, u01, u10, u11);
+        } else if (j < 5) {
+            const uint32_t b = (tid >> j) & 1u;
+            const R cs = b ? u11 : u00, co = b ? u10 : u01;
+#pragma unroll
+            for (int k = 0; k < NR; k++) {
+                const C o = shfl_xor_c(v[k], 1 << j);
+                v[k] = mk(cs * v[k].x + co * o.x, cs * v[k].y + co * o.y);
+            }
+        } else {
+            const uint32_t b = (tid >> j) & 1u;
+            const R cs = b ? u11 : u00, co = b ? u10 : u01;
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < NR; k++)
+                    s[tid + k * kThreads] = v[k];
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < NR; k++) {
+                    const C o = s[(tid ^ (1u << j)) + k * kThreads];
+                    v[k] = mk(cs * v[k].x + co * o.x, cs * v[k].y + co * o.y);
+                }
+            }
+        }
+    };
+    // U: 16 complex values, row-major, read through `get`
+    auto dense2 = [&](uint32_t j0, uint32_t j1, uint32_t p0, uint32_t p1, auto get) {
+        flush();
+        const uint32_t mu = ((mask >> p0) & 1u) | (((mask >> p1) & 1u) << 1);
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                s[tid + k * kThreads] = v[k];
+        }
+        __syncthreads();
+        if (active) {
+            const uint32_t m0b = 1u << j0, m1b = 1u << j1;
+#pragma unroll
+            for (int k = 0; k < NR; k++) {
+                const uint32_t e = tid + (uint32_t)k * kThreads;
+                const uint32_t r = ((e >> j0) & 1u) | (((e >> j1) & 1u) << 1);
+                const uint32_t eb = e & ~(m0b | m1b);
+                C acc2 = mk((R)0, (R)0);
+#pragma unroll
+                for (uint32_t c = 0; c < 4; c++) {
+                    const C x = s[eb | ((c & 1u) ? m0b : 0u) | ((c & 2u) ? m1b : 0u)];
+                    acc2 = cmadd(get((r ^ mu) * 4 + (c ^ mu)), x, acc2);
+                }
+                v[k] = acc2;
+            }
+        }
+    };
+    // one diagonal gate from the per-gate tables (runs holding an X or Y noise event)
+    auto diag_gate = [&](const Instr &I) {
+        const R *M = mats + (size_t)I.gate * 32;
+        const uint32_t fl = I.pad;
+        if (fl & 1u)
+            acc.base = cmul(acc.base, mk(M[0], M[1]));
+        if (fl & 2u)
+            acc_alpha(acc, I.j0, I.p0, xt, mk(M[2], M[3]));
+        if (I.op == OP_DIAG2) {
+            if (fl & 4u)
+                acc_alpha(acc, I.j1, I.p1, xt, mk(M[4], M[5]));
+            if (fl & 8u)
+                acc_gamma(acc, I.j0, I.p0, I.j1, I.p1, xt, mk(M[6], M[7]));
+        }
+        pending = true;
+    };
+    constexpr uint32_t CS = (uint32_t)sizeof(C);
+    if (!zero_tile) {
+        for (uint32_t c = a.chunk_begin; c < a.chunk_end; c++) {
+            const uint32_t o0 = a.chunk_off[c], o1 = a.chunk_off[c + 1];
+            __syncthreads();
+            for (uint32_t x = tid; x < (o1 - o0) / 16u; x += kThreads)
+                reinterpret_cast<uint4 *>(pbuf)[x] = reinterpret_cast<const uint4 *>(a.prog + o0)[x];
+            __syncthreads();
+            uint32_t p = 0;
+            while (p < o1 - o0) {
+                const uint4 hw = *reinterpret_cast<const uint4 *>(pbuf + p);
+                const uint32_t htype = hw.x & 0xffu, ha = (hw.x >> 8) & 0xffu, hb = (hw.x >> 16) & 0xffu,
+                               hc = hw.x >> 24, hd = hw.y & 0xffu, he = (hw.y >> 8) & 0xffu, hsite = hw.y >> 16;
+                const uint32_t hibeg = hw.z, hiend = hw.w;
+                const unsigned char *pay = pbuf + p + 16;
+                auto pc = [&](uint32_t i) -> C { return *reinterpret_cast<const C *>(pay + i * CS); };
+                if (htype == REC_DENSE1) {
+                    if (hc)
+                        dense1_real(ha, hb, pc(0).x, pc(1).x, pc(2).x, pc(3).x);
+                    else
+                        dense1(ha, hb, pc(0), pc(1), pc(2), pc(3));
+                    const uint32_t pz = noise_at(hsite);
+                    if (pz)
+                        apply_noise(pz, 3, ha, hb, ha, hb);
+                    p += 16u + ((4u * CS + 15u) & ~15u);
+                } else if (htype == REC_DENSE2) {
+                    dense2(ha, hb, hc, hd, pc);
+                    const uint32_t pz = noise_at(hsite);
+                    if (pz)
+                        apply_noise(pz, 15, ha, hc, hb, hd);
+                    p += 16u + 16u * CS;
+                } else {
+                    const uint32_t nfac = ha + hb + hc + hd + he;
+                    const uint32_t nsites = hiend - hibeg;
+                    uint32_t any = 0;
+                    for (uint32_t x = 0; x < nsites; x++)
+                        any |= noise_at(hsite + x);
+                    if (!any) {
+                        acc.base = cmul(acc.base, pc(0));
+                        const unsigned char *fp = pay + 16;
+                        constexpr uint32_t FS = CS == 8 ? 16u : 32u;
+                        auto fval = [&](const unsigned char *q) -> C {
+                            return *reinterpret_cast<const C *>(q + (CS == 8 ? 8 : 16));
+                        };
+                        // FacHdr as one 64-bit word: kind | j0<<8 | p0<<16 | j1<<24 | p1<<32
+                        for (uint32_t f = 0; f < ha; f++, fp += FS) {  // a^{x_p}, p fixed
+                            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(fp);
+                            if ((xt >> ((w0 >> 16) & 0xffu)) & 1u)
+                                acc.base = cmul(acc.base, fval(fp));
+                        }
+                        for (uint32_t f = 0; f < hb; f++, fp += FS) {  // a^{x_s}, slot s
+                            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(fp);
+                            acc.mul_E((int)((w0 >> 8) & 0xffu) - 8, fval(fp));
+                        }
+                        for (uint32_t f = 0; f < hc; f++, fp += FS) {  // c^{x_p0 x_p1}, both fixed
+                            const uint2 w = *reinterpret_cast<const uint2 *>(fp);
+                            if ((xt >> ((w.x >> 16) & 0xffu)) & (xt >> (w.y & 0xffu)) & 1u)
+                                acc.base = cmul(acc.base, fval(fp));
+                        }
+                        for (uint32_t f = 0; f < hd; f++, fp += FS) {  // c^{x_p0 x_s1}
+                            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(fp);
+                            if ((xt >> ((w0 >> 16) & 0xffu)) & 1u)
+                                acc.mul_E((int)(w0 >> 24) - 8, fval(fp));
+                        }
+                        for (uint32_t f = 0; f < he; f++, fp += FS) {  // c^{x_s0 x_s1}
+                            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(fp);
+                            acc.mul_Gs((int)((w0 >> 8) & 0xffu) - 8, (int)(w0 >> 24) - 8, fval(fp));
+                        }
+                        pending = true;
+                    } else {
+                        for (uint32_t ii = hibeg; ii < hiend; ii++) {
+                            const Instr I = a.instr[ii];
+                            if (I.op == OP_DIAG1 || I.op == OP_DIAG2)
+                                diag_gate(I);
+                            const uint32_t pz = noise_at(I.site);
+                            if (pz)
+                                apply_noise(pz, I.npaulis, I.j0, I.np0, I.j1, I.np1);
+                        }
+                    }
+                    p += 32u + nfac * (CS == 8 ? 16u : 32u);
+                }
+            }
+        }
+        flush();
     } else {
         mask = m1.mask;
     }
-    __syncthreads();
 
     // ---- epilogue ------------------------------------------------------
     if (MODE == MODE_STORE) {
-        C *dst = reinterpret_cast<C *>(a.out) + (uint64_t)slot * a.state_elems;
-        for (uint32_t e = tid; e < TE; e += kThreads)
-            dst[base | dep[e >> a.L] | (e & lomask)] = s[e];
+        if (active) {
+            C *dst = reinterpret_cast<C *>(a.out) + (uint64_t)slot * a.state_elems;
+            const uint32_t tb0 = base | tphys;
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                dst[tb0 | soff[k]] = v[k];
+        }
         return;
     }
-
     // tile-coordinate frame mask (final frame)
     uint32_t mT = 0;
     for (uint32_t j = 0; j < a.t; j++)
         mT |= ((mask >> a.tbits[j]) & 1u) << j;
+    if (MODE == MODE_SAMPLE) {
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                s[tid + k * kThreads] = v[k];
+        }
+        __syncthreads();
+    }
     const uint32_t G = 1u << SL.gamma;
     auto elem_of_key = [&](uint32_t key) -> uint32_t {
         return ((uint32_t)lut[key & 127] | (uint32_t)lut[128 + ((key >> 7) & 127)]) ^ mT;
     };
 
     if (MODE == MODE_SUMS) {
-        // H-bit part of the global group index of this tile
+        // Block sums of |a|^2 over the 2^gamma amplitudes that differ only in the
+        // tile positions holding the lowest gamma logical bits (mask wpos):
+        // butterfly additions over register slots, then lanes (shuffles), then
+        // warp bits (shared memory), in the state's precision (a pairwise order);
+        // each block sum leaves as one FP64 value.
+        uint32_t wpos = 0;
+        for (uint32_t r = 0; r < SL.gamma; r++)
+            wpos |= 1u << SL.rank_pos[r];
+        R pr[NR];
+#pragma unroll
+        for (int k = 0; k < NR; k++)
+            pr[k] = norm2<R>(v[k]);
+#pragma unroll
+        for (int sb = 0; sb < LOGR; sb++) {
+            if ((wpos >> (8 + sb)) & 1u) {
+#pragma unroll
+                for (int k = 0; k < NR; k++)
+                    if (!((k >> sb) & 1))
+                        pr[k] += pr[k | (1 << sb)];
+            }
+        }
+        for (uint32_t j = 0; j < 5; j++) {
+            if ((wpos >> j) & 1u) {
+#pragma unroll
+                for (int k = 0; k < NR; k++)
+                    pr[k] += __shfl_xor_sync(0xffffffffu, pr[k], 1 << j);
+            }
+        }
+        R *sr = reinterpret_cast<R *>(s);
+        for (uint32_t j = 5; j < 8; j++) {
+            if ((wpos >> j) & 1u) {
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < NR; k++)
+                    sr[tid + k * kThreads] = pr[k];
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < NR; k++)
+                    pr[k] += sr[(tid ^ (1u << j)) + k * kThreads];
+            }
+        }
+        // the representative of each block (all gamma low logical bits physically 0
+        // in tile coordinates) writes it; its block index is its higher logical bits
         uint64_t hpart = 0;
         for (uint32_t b = 0; b < a.n - a.t; b++) {
             const uint32_t pb = a.hbits[b];
             hpart |= (uint64_t)(((base ^ mask) >> pb) & 1u) << (SL.logical_of_hbit[b] - SL.gamma);
         }
-        const uint32_t GPT = TE >> SL.gamma;                 // groups in this tile
-        uint32_t TPG = GPT >= kThreads ? 1u : kThreads / GPT; // threads per group
-        if (TPG > G) TPG = G;
-        const uint32_t KPT = G / TPG;                         // keys per thread
-        const uint32_t nwork = GPT * TPG;
-        for (uint32_t wbase = 0; wbase < nwork; wbase += kThreads) {
-            const uint32_t wi = wbase + tid;
-            double part = 0.0;
-            uint32_t grp = 0;
-            if (wi < nwork) {
-                grp = wi / TPG;
-                const uint32_t k0 = grp * G + (wi % TPG) * KPT;
-                R acc = 0;
-                for (uint32_t k = 0; k < KPT; k++) {
-                    acc += norm2<R>(s[elem_of_key(k0 + k)]);
-                    if (((k + 1) & 15u) == 0) {
-                        part += (double)acc;
-                        acc = 0;
-                    }
-                }
-                part += (double)acc;
-            }
-            // reduce over the TPG consecutive threads of each group
-            if (TPG <= 32) {
-                for (uint32_t off = 1; off < TPG; off <<= 1)
-                    part += __shfl_xor_sync(0xffffffffu, part, off);
-                if (wi < nwork && (wi % TPG) == 0) {
-                    uint64_t g = hpart;
-                    const uint32_t keyhi = grp;  // rank bits >= gamma of this group
-                    for (uint32_t r = SL.gamma; r < a.t; r++)
-                        g |= (uint64_t)((keyhi >> (r - SL.gamma)) & 1u) << (SL.rank_q[r] - SL.gamma);
-                    a.S[(uint64_t)slot * SL.groups + g] = part;
-                }
-            } else {
-                red[tid] = part;
-                __syncthreads();
-                if (wi < nwork && (wi % TPG) == 0) {
-                    double sum = 0.0;
-                    for (uint32_t k = 0; k < TPG; k++)
-                        sum += red[tid + k];
+        if (active && (tid & wpos) == 0) {
+#pragma unroll
+            for (int k = 0; k < NR; k++) {
+                if ((((uint32_t)k << 8) & wpos) == 0) {
+                    const uint32_t e = (tid + (uint32_t)k * kThreads) ^ mT;  // logical tile bits
                     uint64_t g = hpart;
                     for (uint32_t r = SL.gamma; r < a.t; r++)
-                        g |= (uint64_t)((grp >> (r - SL.gamma)) & 1u) << (SL.rank_q[r] - SL.gamma);
-                    a.S[(uint64_t)slot * SL.groups + g] = sum;
+                        g |= (uint64_t)((e >> SL.rank_pos[r]) & 1u) << (SL.rank_q[r] - SL.gamma);
+                    a.S[(uint64_t)slot * SL.groups + g] = (double)pr[k];
                 }
-                __syncthreads();
             }
         }
         return;
@@ -550,8 +933,8 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const __grid_constant__ 
     if (tid < 32) {
         const uint64_t y = (gstar << SL.gamma) | wstar;
         bool flip = false;
-        if ((uint32_t)tid < a.n) {
-            const uint4 rr = draw(a.seed, node, (uint32_t)tid, kDomRead);
+        if (tid < a.n) {
+            const uint4 rr = draw(a.seed, node, tid, kDomRead);
             flip = (uint64_t)rr.x < a.thrm;
         }
         const uint32_t fl = __ballot_sync(0xffffffffu, flip);
@@ -560,16 +943,29 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(const __grid_constant__ 
     }
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, int LOGR>
 static int launch_pass_t(const PassK &k, dim3 grid, size_t smem, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(pass_kernel<R, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(pass_kernel<R, MODE, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    pass_kernel<R, MODE><<<grid, kThreads, smem, st>>>(k);
+    pass_kernel<R, MODE, LOGR><<<grid, kThreads, smem, st>>>(k);
     return (int)cudaGetLastError();
+}
+
+template <typename R, int MODE>
+static int launch_pass_r(const PassK &k, int logr, dim3 grid, size_t smem, cudaStream_t st)
+{
+    switch (logr) {
+    case 0: return launch_pass_t<R, MODE, 0>(k, grid, smem, st);
+    case 1: return launch_pass_t<R, MODE, 1>(k, grid, smem, st);
+    case 2: return launch_pass_t<R, MODE, 2>(k, grid, smem, st);
+    case 3: return launch_pass_t<R, MODE, 3>(k, grid, smem, st);
+    case 4: return launch_pass_t<R, MODE, 4>(k, grid, smem, st);
+    default: return launch_pass_t<R, MODE, 5>(k, grid, smem, st);
+    }
 }
 
 int launch_pass(const PassLaunch &a, void *stream)
@@ -584,6 +980,10 @@ int launch_pass(const PassLaunch &a, void *stream)
     k.parent_lo = a.parent_lo;
     k.arity = a.arity ? a.arity : 1;
     k.instr = a.instr;
+    k.prog = a.prog;
+    k.chunk_off = a.chunk_off;
+    k.chunk_begin = a.chunk_begin;
+    k.chunk_end = a.chunk_end;
     k.mats = a.mats;
     k.noise = a.noise;
     k.meta = a.meta;
@@ -609,20 +1009,23 @@ int launch_pass(const PassLaunch &a, void *stream)
     else
         k.samp = SamplerLayout{};
     const size_t elem = a.fp64 ? 16 : 8;
-    const size_t ndep = ((size_t)1 << (a.t - a.L)) < 4 ? 4 : ((size_t)1 << (a.t - a.L));
-    const size_t smem = ((size_t)1 << a.t) * elem + ndep * 4 + 256 * 2 + kThreads * 8 + 4 * 8;
+    const size_t te = ((size_t)1 << a.t) < (size_t)kThreads ? (size_t)kThreads : ((size_t)1 << a.t);
+    const size_t nzst = ((a.sites < (uint32_t)kNoiseStage ? a.sites : (uint32_t)kNoiseStage) + 15u) / 16u * 16u;
+    const size_t smem = te * elem + 256 * 2 + kThreads * 8 + 4 * 8 + 32 * 4 + nzst + kProgChunkBytes;
+    const int logr = a.t > 8 ? (int)a.t - 8 : 0;
     const uint64_t tiles = (uint64_t)1 << (a.n - a.t);
     dim3 grid = a.mode == MODE_SAMPLE ? dim3(a.nnodes) : dim3((unsigned)tiles, a.nnodes);
     cudaStream_t st = (cudaStream_t)stream;
     if (a.fp64) {
-        if (a.mode == MODE_STORE) return launch_pass_t<double, MODE_STORE>(k, grid, smem, st);
-        if (a.mode == MODE_SUMS) return launch_pass_t<double, MODE_SUMS>(k, grid, smem, st);
-        return launch_pass_t<double, MODE_SAMPLE>(k, grid, smem, st);
+        if (a.mode == MODE_STORE) return launch_pass_r<double, MODE_STORE>(k, logr, grid, smem, st);
+        if (a.mode == MODE_SUMS) return launch_pass_r<double, MODE_SUMS>(k, logr, grid, smem, st);
+        return launch_pass_r<double, MODE_SAMPLE>(k, logr, grid, smem, st);
     }
-    if (a.mode == MODE_STORE) return launch_pass_t<float, MODE_STORE>(k, grid, smem, st);
-    if (a.mode == MODE_SUMS) return launch_pass_t<float, MODE_SUMS>(k, grid, smem, st);
-    return launch_pass_t<float, MODE_SAMPLE>(k, grid, smem, st);
+    if (a.mode == MODE_STORE) return launch_pass_r<float, MODE_STORE>(k, logr, grid, smem, st);
+    if (a.mode == MODE_SUMS) return launch_pass_r<float, MODE_SUMS>(k, logr, grid, smem, st);
+    return launch_pass_r<float, MODE_SAMPLE>(k, logr, grid, smem, st);
 }
+
 
 // ---------------------------------------------------------------------------
 // Utility kernels

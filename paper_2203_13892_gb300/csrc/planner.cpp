@@ -4,6 +4,7 @@
 //   the lowering of every subcircuit into shared-memory tile passes.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <string>
 
@@ -282,6 +283,183 @@ static void choose_tile(uint32_t n, uint32_t tmax, uint32_t need_mask, const uin
     p.L = L;
 }
 
+// Lower every pass into the record program the kernels walk (see RecHdr):
+// dense gates with their matrix inline, and each run of consecutive diagonal
+// gates (lazy SWAPs included) merged into one record of per-qubit and
+// per-pair factors classified by the tile position of their bits.
+static void compile_programs(PlanHost &P)
+{
+    const bool f64 = P.prec == TQS_FP64;
+    const size_t csz = f64 ? 16 : 8, fsz = f64 ? 32 : 16;
+    const size_t kMaxFactors = 200;
+    std::vector<uint8_t> &out = P.prog;
+    out.clear();
+    P.chunk_off.clear();
+    auto put = [&](const void *p, size_t n) {
+        const uint8_t *b = (const uint8_t *)p;
+        out.insert(out.end(), b, b + n);
+    };
+    auto putc = [&](std::complex<double> z) {
+        if (f64) {
+            double v[2] = {z.real(), z.imag()};
+            put(v, 16);
+        } else {
+            float v[2] = {(float)z.real(), (float)z.imag()};
+            put(v, 8);
+        }
+    };
+    auto pad16 = [&]() {
+        while (out.size() % 16)
+            out.push_back(0);
+    };
+    auto cplx = [&](uint32_t gate, int k) {
+        return std::complex<double>(P.mats64[(size_t)gate * 32 + 2 * k], P.mats64[(size_t)gate * 32 + 2 * k + 1]);
+    };
+    size_t chunk_start = 0;
+    auto reserve = [&](size_t bytes) {  // open a new chunk if `bytes` do not fit the current one
+        if (out.size() > chunk_start && out.size() - chunk_start + bytes > (size_t)kProgChunkBytes) {
+            P.chunk_off.push_back((uint32_t)out.size());
+            chunk_start = out.size();
+        }
+    };
+    for (Pass &ps : P.passes) {
+        uint8_t pos[32];
+        std::memset(pos, 0xff, sizeof(pos));
+        for (uint32_t j = 0; j < ps.t; j++)
+            pos[ps.tbits[j]] = (uint8_t)j;
+        auto is_slot = [&](uint8_t p) { return pos[p] != 0xff && pos[p] >= 8; };
+        ps.chunk_begin = (uint32_t)P.chunk_off.size();
+        if (ps.ibeg < ps.iend) {
+            P.chunk_off.push_back((uint32_t)out.size());
+            chunk_start = out.size();
+        }
+        uint32_t k = ps.ibeg;
+        while (k < ps.iend) {
+            const Instr &in = P.instrs[k];
+            if (in.op == OP_DENSE1 || in.op == OP_DENSE2) {
+                const bool two = in.op == OP_DENSE2;
+                reserve(16 + (two ? 16 : 4) * csz);
+                RecHdr h;
+                std::memset(&h, 0, sizeof(h));
+                h.type = two ? REC_DENSE2 : REC_DENSE1;
+                h.a = in.j0;
+                h.b = two ? in.j1 : in.p0;
+                h.c = in.p0;
+                h.d = in.p1;
+                h.site = in.site;
+                h.ibeg = k;
+                h.iend = k + 1;
+                if (!two) {
+                    bool real = true;
+                    for (int e = 0; e < 4; e++)
+                        real = real && cplx(in.gate, e).imag() == 0.0;
+                    h.c = real ? 1 : 0;
+                }
+                put(&h, 16);
+                for (int e = 0; e < (two ? 16 : 4); e++)
+                    putc(cplx(in.gate, e));
+                pad16();
+                k++;
+                continue;
+            }
+            // a run of diagonal gates / lazy SWAPs, cut so that its factors stay bounded
+            std::complex<double> G = 1.0;
+            std::complex<double> alpha[32];
+            for (auto &a : alpha)
+                a = 1.0;
+            std::vector<std::pair<std::pair<uint8_t, uint8_t>, std::complex<double>>> pairs;
+            auto pair_mul = [&](uint8_t a, uint8_t b, std::complex<double> f) {
+                if (a > b)
+                    std::swap(a, b);
+                for (auto &e : pairs)
+                    if (e.first.first == a && e.first.second == b) {
+                        e.second *= f;
+                        return;
+                    }
+                pairs.push_back({{a, b}, f});
+            };
+            const uint32_t r0 = k;
+            while (k < ps.iend && P.instrs[k].op != OP_DENSE1 && P.instrs[k].op != OP_DENSE2 &&
+                   pairs.size() + 32 < kMaxFactors) {
+                const Instr &d = P.instrs[k];
+                if (d.op == OP_DIAG1 || d.op == OP_DIAG2) {
+                    G *= cplx(d.gate, 0);
+                    alpha[d.p0] *= cplx(d.gate, 1);
+                    if (d.op == OP_DIAG2) {
+                        alpha[d.p1] *= cplx(d.gate, 2);
+                        if (d.pad & 8u)
+                            pair_mul(d.p0, d.p1, cplx(d.gate, 3));
+                    }
+                }
+                k++;
+            }
+            std::vector<std::pair<FacHdr, std::complex<double>>> facs;
+            for (uint32_t q = 0; q < 32; q++) {
+                if (alpha[q] == std::complex<double>(1.0, 0.0))
+                    continue;
+                FacHdr f;
+                std::memset(&f, 0, sizeof(f));
+                f.kind = is_slot((uint8_t)q) ? FAC_A_SLOT : FAC_A_FIXED;
+                f.p0 = (uint8_t)q;
+                f.j0 = pos[q];
+                facs.push_back({f, alpha[q]});
+            }
+            for (auto &e : pairs) {
+                if (e.second == std::complex<double>(1.0, 0.0))
+                    continue;
+                uint8_t a = e.first.first, b = e.first.second;
+                FacHdr f;
+                std::memset(&f, 0, sizeof(f));
+                const bool sa = is_slot(a), sb = is_slot(b);
+                if (!sa && !sb)
+                    f.kind = FAC_C_FIXED;
+                else if (sa && sb)
+                    f.kind = FAC_C_SLOTS;
+                else {
+                    f.kind = FAC_C_MIXED;
+                    if (sa)
+                        std::swap(a, b);  // p0 fixed, p1 on a slot
+                }
+                f.p0 = a;
+                f.j0 = pos[a];
+                f.p1 = b;
+                f.j1 = pos[b];
+                facs.push_back({f, e.second});
+            }
+            std::stable_sort(facs.begin(), facs.end(),
+                             [](const std::pair<FacHdr, std::complex<double>> &x,
+                                const std::pair<FacHdr, std::complex<double>> &y) { return x.first.kind < y.first.kind; });
+            uint8_t cnt[8] = {0};
+            for (auto &f : facs)
+                cnt[f.first.kind]++;
+            reserve(32 + facs.size() * fsz + 16);
+            RecHdr h;
+            std::memset(&h, 0, sizeof(h));
+            h.type = REC_RUN;
+            h.a = cnt[FAC_A_FIXED];
+            h.b = cnt[FAC_A_SLOT];
+            h.c = cnt[FAC_C_FIXED];
+            h.d = cnt[FAC_C_MIXED];
+            h.e = cnt[FAC_C_SLOTS];
+            h.site = P.instrs[r0].site;
+            h.ibeg = r0;
+            h.iend = k;
+            put(&h, 16);
+            putc(G);
+            pad16();
+            for (auto &f : facs) {
+                put(&f.first, 8);
+                if (f64)
+                    out.insert(out.end(), 8, 0);  // the value sits 16-byte aligned
+                putc(f.second);
+            }
+            pad16();
+        }
+        ps.chunk_end = (uint32_t)P.chunk_off.size();
+    }
+    P.chunk_off.push_back((uint32_t)out.size());
+}
+
 std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const tqs_options &o,
                        const std::vector<uint64_t> &arity, const std::vector<uint32_t> &split,
                        PlanHost &P)
@@ -305,6 +483,7 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
     // lowered matrices: dense gates keep the full matrix, diagonal gates their diagonal
     P.mats64.assign((size_t)std::max<uint32_t>(G, 1) * 32, 0.0);
     std::vector<uint8_t> op(G);
+    std::vector<uint16_t> diag_flags(G, 0);
     for (uint32_t g = 0; g < G; g++) {
         const Gate &gt = c.gates[g];
         bool two = is_two_qubit(gt.kind);
@@ -323,11 +502,25 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
                         diag = false;
         }
         if (diag) {
+            // D[x] (x = local index) as G * a0^{x0} * a1^{x1} * c^{x0 x1}: the
+            // kernels fold runs of diagonal gates into these factors
             op[g] = two ? OP_DIAG2 : OP_DIAG1;
-            for (int r = 0; r < d; r++) {
-                dst[2 * r] = gt.m[2 * (r * d + r)];
-                dst[2 * r + 1] = gt.m[2 * (r * d + r) + 1];
+            std::complex<double> dd[4];
+            for (int r = 0; r < d; r++)
+                dd[r] = {gt.m[2 * (r * d + r)], gt.m[2 * (r * d + r) + 1]};
+            std::complex<double> f[4] = {dd[0], dd[1] / dd[0], 1.0, 1.0};
+            if (two) {
+                f[2] = dd[2] / dd[0];
+                f[3] = dd[3] * dd[0] / (dd[1] * dd[2]);
             }
+            uint16_t flags = 0;
+            for (int k = 0; k < 4; k++) {
+                dst[2 * k] = f[k].real();
+                dst[2 * k + 1] = f[k].imag();
+                if (f[k] != std::complex<double>(1.0, 0.0))
+                    flags |= (uint16_t)(1u << k);
+            }
+            diag_flags[g] = flags;
         } else {
             op[g] = two ? OP_DENSE2 : OP_DENSE1;
             std::memcpy(dst, gt.m, sizeof(double) * 2 * d * d);
@@ -413,6 +606,7 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
                 in.np1 = low[k].np1;
                 in.npaulis = is_two_qubit(c.gates[k].kind) ? 15 : 3;
                 in.site = (uint16_t)(k - lv.g0);
+                in.pad = diag_flags[k];
                 in.gate = k;
                 P.instrs.push_back(in);
             }
@@ -475,6 +669,7 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
     for (uint32_t r = 0; r < S.gamma; r++)
         if (S.rank_q[r] != r)
             return "internal: sampler layout invariant broken";
+    compile_programs(P);
     return "";
 }
 

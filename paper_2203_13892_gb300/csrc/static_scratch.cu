@@ -139,6 +139,11 @@ extern "C" tqs_status tqs_simulate_static(const tqs_circuit *c, const tqs_noise 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dp.d_pass_start, dp.pst_host.data(), 4 * dp.pst_host.size(), cudaMemcpyHostToDevice,
                             dp.stream);
+    if (e == cudaSuccess && !H.prog.empty())
+        e = cudaMemcpyAsync(dp.d_prog, H.prog.data(), H.prog.size(), cudaMemcpyHostToDevice, dp.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dp.d_chunk_off, H.chunk_off.data(), 4 * H.chunk_off.size(), cudaMemcpyHostToDevice,
+                            dp.stream);
     uint8_t perm[32] = {0};
     for (uint32_t q = 0; q < H.n; q++)
         perm[q] = H.levels.back().perm[q];
