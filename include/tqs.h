@@ -102,6 +102,7 @@ typedef enum {
 
 #define TQS_FLAG_NO_FIDELITY 0x1u /* skip the ideal run and the fidelity (fidelity = NaN) */
 #define TQS_FLAG_PROFILE 0x2u     /* time every launch with CUDA events (report.prof_*) */
+#define TQS_FLAG_AUTOTUNE 0x4u    /* choose tile_qubits by timing trial runs (cached per circuit shape) */
 
 /* Kernel classes timed under TQS_FLAG_PROFILE (index into report.prof_*). */
 #define TQS_PROF_NOISE 0   /* Philox noise draws + Pauli frames */
@@ -119,7 +120,8 @@ typedef enum {
  *   tile_qubits  maximum shared-memory tile width t in [6, 13] (0 = default: 12 FP32, 11 FP64)
  *   batch        node instances per launch (0 = chosen from the memory budget)
  *   workspace, workspace_bytes   optional caller-owned DEVICE buffer (>= 256-byte
- *                aligned) used for all scratch; NULL = the library allocates
+ *                aligned) used for all scratch; NULL = the library allocates, at
+ *                most workspace_bytes when that is nonzero
  *   stream       cudaStream_t to run on (NULL = legacy default stream)
  *   flags        TQS_FLAG_* bits */
 typedef struct {
@@ -188,6 +190,24 @@ tqs_status tqs_plan_create(const tqs_circuit *c, const tqs_noise *nz, uint64_t s
 tqs_status tqs_plan_execute(tqs_plan *p, uint64_t seed, uint64_t *d_counts, tqs_report *report);
 size_t tqs_plan_workspace_bytes(const tqs_plan *p);
 void tqs_plan_destroy(tqs_plan *p);
+
+/* Batched execution (many independent simulations, uneven sizes).  All
+ * circuits are planned with the shared options (not EXPLICIT; workspace must be
+ * NULL: the batch shares out device memory in proportion to 2^n), then their
+ * launches are captured once into a CUDA graph with one branch per circuit.
+ * tqs_batch_execute writes seeds[i] to device memory and replays the graph on the
+ * batch's own stream (it returns after the replay finished); histogram i is then
+ * read with tqs_batch_counts (HOST copy) or tqs_batch_device_counts (device
+ * pointer, valid until the next execute or destroy).  The report, when given,
+ * aggregates all circuits. */
+typedef struct tqs_batch tqs_batch;
+tqs_status tqs_batch_create(size_t count, const tqs_circuit *const *circuits, const tqs_noise *const *noises,
+                            const uint64_t *shots, const tqs_options *opts, tqs_batch **out);
+tqs_status tqs_batch_execute(tqs_batch *b, const uint64_t *seeds, tqs_report *report);
+tqs_status tqs_batch_counts(const tqs_batch *b, size_t i, uint64_t *counts);
+const uint64_t *tqs_batch_device_counts(const tqs_batch *b, size_t i);
+size_t tqs_batch_size(const tqs_batch *b);
+void tqs_batch_destroy(tqs_batch *b);
 
 /* Debug / parity entry points.
  * tqs_debug_node_state: the logical state (2^n complex, interleaved FP64, HOST

@@ -8,6 +8,12 @@ PyTorch-owned device memory and streams.
 from . import capi  # noqa: F401
 from .capi import (  # noqa: F401
     TqsError,
+    tqs_batch_counts,
+    tqs_batch_create,
+    tqs_batch_destroy,
+    tqs_batch_device_counts,
+    tqs_batch_execute,
+    tqs_batch_size,
     circuit,
     options,
     tqs_abi_version,

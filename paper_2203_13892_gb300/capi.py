@@ -22,6 +22,7 @@ TQS_FP64, TQS_FP32 = 0, 1
 TQS_PART_DCP, TQS_PART_UCP, TQS_PART_XCP, TQS_PART_EXPLICIT, TQS_PART_LEARNED = range(5)
 TQS_FLAG_NO_FIDELITY = 0x1
 TQS_FLAG_PROFILE = 0x2
+TQS_FLAG_AUTOTUNE = 0x4
 TQS_MAX_LEVELS = 17
 TQS_PROF_KINDS = 4
 PROF_NAMES = ("noise", "store", "sums", "sample")
@@ -85,7 +86,8 @@ EXPORTS = (
     "tqs_options_default", "tqs_partition", "tqs_simulate", "tqs_plan_create",
     "tqs_plan_execute", "tqs_plan_workspace_bytes", "tqs_plan_destroy",
     "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_simulate_static", "tqs_last_error",
-    "tqs_abi_version",
+    "tqs_abi_version", "tqs_batch_create", "tqs_batch_execute", "tqs_batch_counts",
+    "tqs_batch_device_counts", "tqs_batch_size", "tqs_batch_destroy",
 )
 TQS_STATIC_SCRATCH_BYTES = 32 << 20
 
@@ -128,6 +130,18 @@ def lib():
             L.tqs_debug_node_noise.restype = st
             L.tqs_simulate_static.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.POINTER(tqs_options), vp]
             L.tqs_simulate_static.restype = st
+            L.tqs_batch_create.argtypes = [C.c_size_t, C.POINTER(vp), C.POINTER(vp), u64p, C.POINTER(tqs_options),
+                                           C.POINTER(vp)]
+            L.tqs_batch_create.restype = st
+            L.tqs_batch_execute.argtypes = [vp, u64p, C.POINTER(tqs_report)]
+            L.tqs_batch_execute.restype = st
+            L.tqs_batch_counts.argtypes = [vp, C.c_size_t, u64p]
+            L.tqs_batch_counts.restype = st
+            L.tqs_batch_device_counts.argtypes = [vp, C.c_size_t]
+            L.tqs_batch_device_counts.restype = C.c_void_p
+            L.tqs_batch_size.argtypes = [vp]
+            L.tqs_batch_size.restype = C.c_size_t
+            L.tqs_batch_destroy.argtypes = [vp]
             L.tqs_last_error.restype = C.c_char_p
             L.tqs_abi_version.restype = C.c_int
             _lib = L
@@ -305,3 +319,50 @@ def tqs_simulate_static(c: Handle, nz: Handle, shots: int, seed: int, opts: Opti
     allocation); d_counts is the device address of a 2^n uint64 histogram."""
     _check(lib().tqs_simulate_static(c.ptr, nz.ptr, int(shots), int(seed), C.byref(opts) if opts else None,
                                      C.c_void_p(int(d_counts))))
+
+
+class Batch(Handle):
+    """A tqs_batch plus the handles it was built from (kept alive)."""
+
+    def __init__(self, ptr, keep, sizes):
+        super().__init__(ptr, lib().tqs_batch_destroy)
+        self._keep = keep
+        self.sizes = sizes
+
+
+def tqs_batch_create(circuits, noises, shots, opts: Optional[tqs_options] = None) -> Batch:
+    """circuits, noises: sequences of Handles; shots: sequence of ints."""
+    n = len(circuits)
+    ca = (C.c_void_p * n)(*[c.ptr for c in circuits])
+    na = (C.c_void_p * n)(*[z.ptr for z in noises])
+    sa = np.ascontiguousarray(shots, dtype=np.uint64)
+    out = C.c_void_p()
+    _check(lib().tqs_batch_create(n, ca, na, sa.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                  C.byref(opts) if opts else None, C.byref(out)))
+    return Batch(out.value, (list(circuits), list(noises)), None)
+
+
+def tqs_batch_execute(b: Batch, seeds, report: bool = False):
+    sa = np.ascontiguousarray(seeds, dtype=np.uint64)
+    rep = tqs_report() if report else None
+    _check(lib().tqs_batch_execute(b.ptr, sa.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                   C.byref(rep) if rep is not None else None))
+    return rep.as_dict() if rep is not None else None
+
+
+def tqs_batch_counts(b: Batch, i: int, n: int) -> np.ndarray:
+    out = np.zeros(1 << n, dtype=np.uint64)
+    _check(lib().tqs_batch_counts(b.ptr, int(i), out.ctypes.data_as(C.POINTER(C.c_uint64))))
+    return out
+
+
+def tqs_batch_device_counts(b: Batch, i: int) -> int:
+    return int(lib().tqs_batch_device_counts(b.ptr, int(i)) or 0)
+
+
+def tqs_batch_size(b: Batch) -> int:
+    return int(lib().tqs_batch_size(b.ptr))
+
+
+def tqs_batch_destroy(b: Batch) -> None:
+    b.close()

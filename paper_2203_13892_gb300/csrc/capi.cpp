@@ -11,15 +11,6 @@
 #include "executor.h"
 #include "handles.h"
 
-struct tqs_plan {
-    tqs::Circuit c;
-    tqs::Noise nz;
-    uint64_t shots = 0;
-    std::vector<uint64_t> arity;
-    std::vector<uint32_t> split;
-    tqs::DevicePlan dp;
-};
-
 namespace {
 thread_local std::string g_err;
 
@@ -47,9 +38,8 @@ tqs_options opts_or_default(const tqs_options *o)
     return d;
 }
 
-// Partition + lower + upload.  store_leaves keeps every level's states.
-tqs_status make_plan(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options &o,
-                     bool store_leaves, std::unique_ptr<tqs_plan> &out)
+tqs_status make_plan_once(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options &o,
+                          bool store_leaves, std::unique_ptr<tqs_plan> &out)
 {
     if (!c || !nz)
         return fail(TQS_EINVAL, "circuit and noise handles are required");
@@ -123,7 +113,7 @@ tqs_status fidelity(const tqs_circuit *c, uint64_t shots, const unsigned long lo
     o.stream = stream;
     o.batch = 1;
     std::unique_ptr<tqs_plan> ip;
-    tqs_status st = make_plan(c, &quiet, 1, o, true, ip);
+    tqs_status st = make_plan_once(c, &quiet, 1, o, true, ip);
     if (st != TQS_OK)
         return st;
     std::string err;
@@ -147,6 +137,19 @@ tqs_status fidelity(const tqs_circuit *c, uint64_t shots, const unsigned long lo
 }  // namespace
 
 tqs_status tqs::set_error(tqs_status s, const std::string &msg) { return fail(s, msg); }
+
+tqs_status tqs::make_plan(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options &o,
+                          bool store_leaves, std::unique_ptr<tqs_plan> &out)
+{
+    if (!(o.flags & TQS_FLAG_AUTOTUNE) || store_leaves)
+        return make_plan_once(c, nz, shots, o, store_leaves, out);
+    tqs_options tuned = o;
+    tqs_status st = tqs::autotune(c, nz, shots, o, tuned);
+    if (st != TQS_OK)
+        return st;
+    tuned.flags &= ~TQS_FLAG_AUTOTUNE;
+    return make_plan_once(c, nz, shots, tuned, store_leaves, out);
+}
 
 extern "C" {
 
@@ -225,7 +228,7 @@ tqs_status tqs_plan_create(const tqs_circuit *c, const tqs_noise *nz, uint64_t s
     if (!out)
         return fail(TQS_EINVAL, "out is NULL");
     std::unique_ptr<tqs_plan> p;
-    tqs_status st = make_plan(c, nz, shots, opts_or_default(opts), false, p);
+    tqs_status st = tqs::make_plan(c, nz, shots, opts_or_default(opts), false, p);
     if (st != TQS_OK)
         return st;
     *out = p.release();
@@ -263,7 +266,7 @@ tqs_status tqs_simulate(const tqs_circuit *c, const tqs_noise *nz, uint64_t shot
         return fail(TQS_EINVAL, "counts is NULL");
     tqs_options o = opts_or_default(opts);
     std::unique_ptr<tqs_plan> p;
-    tqs_status st = make_plan(c, nz, shots, o, false, p);
+    tqs_status st = tqs::make_plan(c, nz, shots, o, false, p);
     if (st != TQS_OK)
         return st;
     std::string err;
@@ -303,7 +306,7 @@ tqs_status tqs_debug_node_state(const tqs_circuit *c, const tqs_noise *nz, uint6
     tqs_options o = opts_or_default(opts);
     o.batch = 1;
     std::unique_ptr<tqs_plan> p;
-    tqs_status st = make_plan(c, nz, shots, o, true, p);
+    tqs_status st = make_plan_once(c, nz, shots, o, true, p);
     if (st != TQS_OK)
         return st;
     const tqs::PlanHost &H = p->dp.host;
@@ -361,7 +364,7 @@ tqs_status tqs_debug_node_noise(const tqs_circuit *c, const tqs_noise *nz, uint6
     tqs_options o = opts_or_default(opts);
     o.batch = 1;
     std::unique_ptr<tqs_plan> p;
-    tqs_status st = make_plan(c, nz, shots, o, true, p);
+    tqs_status st = make_plan_once(c, nz, shots, o, true, p);
     if (st != TQS_OK)
         return st;
     const tqs::PlanHost &H = p->dp.host;

@@ -158,6 +158,8 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot));
         budget = (size_t)(0.75 * (double)fr);
+        if (o.workspace_bytes && o.workspace_bytes < budget)
+            budget = o.workspace_bytes;  // a cap on what the library allocates
         budget = budget > fixed ? budget - fixed : 0;
     }
     uint64_t B = std::min<uint64_t>(want, budget / std::max<size_t>(per_slot, 1));
@@ -233,6 +235,7 @@ tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vect
     nl.noise_out = noise[i];
     nl.meta_out = meta[i];
     nl.seed = seed;
+    nl.seed_dev = seed_dev;
     nl.thr1 = H.thr1;
     nl.thr2 = H.thr2;
     CKP(TQS_PROF_NOISE, (double)nn * (nl.sites + 8.0 * (np + 1)), launch_noise(nl, stream));
@@ -273,6 +276,7 @@ tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vect
         a.samp = &H.samp;
         a.counts = counts;
         a.seed = seed;
+        a.seed_dev = seed_dev;
         a.thrm = H.thrm;
         // state bytes a pass must move: read its input (nothing when it starts
         // from |0...0>) and, unless it only measures, write its output
@@ -359,6 +363,7 @@ tqs_status DevicePlan::run_chain(uint32_t level, uint64_t node, uint64_t seed, s
         nl.noise_out = noise[i];
         nl.meta_out = meta[i];
         nl.seed = seed;
+        nl.seed_dev = nullptr;
         nl.thr1 = H.thr1;
         nl.thr2 = H.thr2;
         CKL(launch_noise(nl, stream));

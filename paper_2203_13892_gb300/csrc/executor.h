@@ -17,6 +17,7 @@ struct DevicePlan {
     tqs_options opts{};
     cudaStream_t stream = nullptr;
     bool store_leaves = false;  // keep leaf states (debug chains)
+    const uint64_t *seed_dev = nullptr;  // device seed read by the kernels (graph replays)
     uint64_t batch = 0;         // node instances per chunk and level
     void *ws = nullptr;
     size_t ws_bytes = 0;

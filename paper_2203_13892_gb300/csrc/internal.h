@@ -175,6 +175,7 @@ struct NoiseLaunch {
     uint64_t parent_lo, arity;
     uint8_t *noise_out;        // [slot][sites]
     NodeMeta *meta_out;        // [slot][npass + 1]
+    const uint64_t *seed_dev;  // when non-null the seed is read here (graph replays)
     uint64_t seed, thr1, thr2;
 };
 int launch_noise(const NoiseLaunch &a, void *stream);
@@ -206,9 +207,12 @@ struct PassLaunch {
     double *S;                 // SUMS / SAMPLE block sums
     const SamplerLayout *samp; // copied by value into the kernel parameters
     unsigned long long *counts;
+    const uint64_t *seed_dev;  // when non-null the seed is read here (graph replays)
     uint64_t seed, thrm;
 };
 int launch_pass(const PassLaunch &a, void *stream);
+// Sets the shared-memory limits of every kernel variant (call before a stream capture).
+int prepare_kernels();
 
 int launch_fill_u64(unsigned long long *p, uint64_t n, void *stream);
 

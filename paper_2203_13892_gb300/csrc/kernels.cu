@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) noise_kernel(const __grid_constant__ Nois
     if (w >= a.nnodes)
         return;
     const uint64_t node = a.node_lo + w;
+    const uint64_t seed = a.seed_dev ? *a.seed_dev : a.seed;
     NodeMeta par = {0u, 0u};
     if (a.parent_meta) {
         const uint64_t ps = node / a.arity - a.parent_lo;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(256) noise_kernel(const __grid_constant__ Nois
         if (s < a.sites) {
             const Instr I = a.instr[s];
             const uint64_t thr = I.npaulis == 15 ? a.thr2 : a.thr1;
-            const uint4 r = draw(a.seed, node, I.gate, kDomNoise);
+            const uint4 r = draw(seed, node, I.gate, kDomNoise);
             uint32_t pz = 0;
             if ((uint64_t)r.x < thr)
                 pz = 1u + (uint32_t)(((uint64_t)r.y * I.npaulis) >> 32);
@@ -159,6 +160,7 @@ struct PassK {
     const NodeMeta *meta;
     double *S;
     unsigned long long *counts;
+    const uint64_t *seed_dev;
     uint64_t seed, thrm;
     uint32_t ibeg, iend, n, t, L, sites, meta_stride, pass_local;
     uint32_t chunk_begin, chunk_end;
@@ -480,6 +482,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
 
     const uint32_t slot = (MODE == MODE_SAMPLE) ? blockIdx.x : blockIdx.y;
     const uint64_t node = a.node_lo + slot;
+    const uint64_t seed = a.seed_dev ? *a.seed_dev : a.seed;
     const NodeMeta m0 = a.meta[(uint64_t)slot * a.meta_stride + a.pass_local];
     const NodeMeta m1 = a.meta[(uint64_t)slot * a.meta_stride + a.pass_local + 1];
 
@@ -523,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     } else {
         // stage 1: the block of 2^gamma outcomes, from this leaf's block sums
         const double *Sl = a.S + (uint64_t)slot * SL.groups;
-        const uint4 r = draw(a.seed, node, 0u, kDomMeas);
+        const uint4 r = draw(seed, node, 0u, kDomMeas);
         const double u = ((double)(r.x >> 5) * 67108864.0 + (double)(r.y >> 6)) * (1.0 / 9007199254740992.0);
         const uint64_t chunk = (SL.groups + kThreads - 1) / kThreads;
         double local = 0.0;
@@ -934,7 +937,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
         const uint64_t y = (gstar << SL.gamma) | wstar;
         bool flip = false;
         if (tid < a.n) {
-            const uint4 rr = draw(a.seed, node, tid, kDomRead);
+            const uint4 rr = draw(seed, node, tid, kDomRead);
             flip = (uint64_t)rr.x < a.thrm;
         }
         const uint32_t fl = __ballot_sync(0xffffffffu, flip);
@@ -943,16 +946,40 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     }
 }
 
+template <typename R, int MODE, int LOGR> static int set_pass_attr()
+{
+    return (int)cudaFuncSetAttribute(pass_kernel<R, MODE, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     200 * 1024);
+}
+
 template <typename R, int MODE, int LOGR>
 static int launch_pass_t(const PassK &k, dim3 grid, size_t smem, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(pass_kernel<R, MODE, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        set_pass_attr<R, MODE, LOGR>();
         attr = true;
     }
     pass_kernel<R, MODE, LOGR><<<grid, kThreads, smem, st>>>(k);
     return (int)cudaGetLastError();
+}
+
+template <typename R, int MODE> static int set_attrs_r()
+{
+    int e = set_pass_attr<R, MODE, 0>();
+    e |= set_pass_attr<R, MODE, 1>();
+    e |= set_pass_attr<R, MODE, 2>();
+    e |= set_pass_attr<R, MODE, 3>();
+    e |= set_pass_attr<R, MODE, 4>();
+    e |= set_pass_attr<R, MODE, 5>();
+    return e;
+}
+
+int prepare_kernels()
+{
+    int e = set_attrs_r<float, MODE_STORE>() | set_attrs_r<float, MODE_SUMS>() | set_attrs_r<float, MODE_SAMPLE>();
+    e |= set_attrs_r<double, MODE_STORE>() | set_attrs_r<double, MODE_SUMS>() | set_attrs_r<double, MODE_SAMPLE>();
+    return e;
 }
 
 template <typename R, int MODE>
@@ -990,6 +1017,7 @@ int launch_pass(const PassLaunch &a, void *stream)
     k.S = a.S;
     k.counts = a.counts;
     k.seed = a.seed;
+    k.seed_dev = a.seed_dev;
     k.thrm = a.thrm;
     k.ibeg = a.ibeg;
     k.iend = a.iend;
