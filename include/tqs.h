@@ -97,7 +97,7 @@ typedef enum {
     TQS_PART_UCP = 1,      /* uniform: k+1 levels of equal arity (Sec. 3.2.1) */
     TQS_PART_XCP = 2,      /* exponential: A_i = a * 2^(k-i) (Sec. 3.2.1) */
     TQS_PART_EXPLICIT = 3, /* caller's arity[] and split[] */
-    TQS_PART_LEARNED = 4   /* reserved: currently EUNSUPPORTED */
+    TQS_PART_LEARNED = 4   /* learned partitioner (tqs_learned_set_model), DCP as fallback */
 } tqs_partitioner;
 
 #define TQS_FLAG_NO_FIDELITY 0x1u /* skip the ideal run and the fidelity (fidelity = NaN) */
@@ -208,6 +208,42 @@ tqs_status tqs_batch_counts(const tqs_batch *b, size_t i, uint64_t *counts);
 const uint64_t *tqs_batch_device_counts(const tqs_batch *b, size_t i);
 size_t tqs_batch_size(const tqs_batch *b);
 void tqs_batch_destroy(tqs_batch *b);
+
+/* Learned partitioner (an addition to the paper, which has DCP only).  A small
+ * network (TQS_LEARNED_FEATURES -> 128 -> 128 -> TQS_LEARNED_CLASSES, ReLU,
+ * softmax, FP32, trained and run on the GPU by the library's own kernels)
+ * chooses between candidate trees; class = 10*mode + k means k extra levels with
+ * DCP's first-level sample-size rule (Sec. 3.2, Eq. sample_size_formula) and
+ * equal lower arities, cut into equal parts (mode 0) or with every cut moved to
+ * the nearest tile-pass boundary (mode 1).  DCP is the fallback and the judge: a
+ * class is allowed only when its first-level arity A_0 is at least DCP's (no
+ * wider Hoeffding bound on A_0) and it has no more levels than DCP; with no model
+ * loaded, TQS_PART_LEARNED returns TQS_EUNSUPPORTED.
+ * Parameters: one float array of tqs_learned_param_count() values, laid out
+ * W1[F][128], b1[128], W2[128][128], b2[128], W3[128][C], b3[C]. */
+#define TQS_LEARNED_FEATURES 40
+#define TQS_LEARNED_CLASSES 20
+size_t tqs_learned_param_count(void);
+/* Host only: features (HOST float[TQS_LEARNED_FEATURES]) and, when non-NULL,
+ * allowed[TQS_LEARNED_CLASSES] (1 = valid and judged acceptable against DCP). */
+tqs_status tqs_learned_features(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
+                                float *features, uint8_t *allowed);
+/* Host only: the tree of candidate class `cls` (EINVAL if that class is invalid here). */
+tqs_status tqs_learned_candidate(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
+                                 uint32_t cls, uint32_t *levels_out, uint64_t *arity_out, uint32_t *split_out);
+/* Training with Adam on the GPU: X HOST [rows][F], labels HOST [rows] in
+ * [0, C); mini-batches of `batch` rows, `epochs` passes, learning rate lr;
+ * init = NULL for a seeded He initialisation.  weights: HOST output. */
+tqs_status tqs_learned_train(const float *X, const int32_t *labels, size_t rows, uint32_t epochs, uint32_t batch,
+                             float lr, uint64_t seed, const float *init, float *weights, float *final_loss);
+/* One forward + backward on the GPU: mean cross-entropy and its gradient (HOST
+ * arrays; grad has tqs_learned_param_count() floats). */
+tqs_status tqs_learned_loss_grad(const float *weights, const float *X, const int32_t *labels, size_t rows,
+                                 float *loss, float *grad);
+/* Forward on the GPU: logits HOST [rows][C]. */
+tqs_status tqs_learned_predict(const float *weights, const float *X, size_t rows, float *logits);
+/* Process-wide model used by TQS_PART_LEARNED (copied); NULL unloads it. */
+tqs_status tqs_learned_set_model(const float *weights);
 
 /* Debug / parity entry points.
  * tqs_debug_node_state: the logical state (2^n complex, interleaved FP64, HOST

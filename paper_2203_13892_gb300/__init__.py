@@ -22,6 +22,13 @@ from .capi import (  # noqa: F401
     tqs_debug_node_noise,
     tqs_debug_node_state,
     tqs_last_error,
+    tqs_learned_candidate,
+    tqs_learned_features,
+    tqs_learned_loss_grad,
+    tqs_learned_param_count,
+    tqs_learned_predict,
+    tqs_learned_set_model,
+    tqs_learned_train,
     tqs_noise_destroy,
     tqs_noise_model,
     tqs_options_default,

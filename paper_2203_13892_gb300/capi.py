@@ -87,8 +87,12 @@ EXPORTS = (
     "tqs_plan_execute", "tqs_plan_workspace_bytes", "tqs_plan_destroy",
     "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_simulate_static", "tqs_last_error",
     "tqs_abi_version", "tqs_batch_create", "tqs_batch_execute", "tqs_batch_counts",
-    "tqs_batch_device_counts", "tqs_batch_size", "tqs_batch_destroy",
+    "tqs_batch_device_counts", "tqs_batch_size", "tqs_batch_destroy", "tqs_learned_param_count",
+    "tqs_learned_features", "tqs_learned_candidate", "tqs_learned_train", "tqs_learned_loss_grad",
+    "tqs_learned_predict", "tqs_learned_set_model",
 )
+TQS_LEARNED_FEATURES = 40
+TQS_LEARNED_CLASSES = 20
 TQS_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -142,6 +146,22 @@ def lib():
             L.tqs_batch_size.argtypes = [vp]
             L.tqs_batch_size.restype = C.c_size_t
             L.tqs_batch_destroy.argtypes = [vp]
+            fp, i32p, u8p = C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_uint8)
+            L.tqs_learned_param_count.restype = C.c_size_t
+            L.tqs_learned_features.argtypes = [vp, vp, C.c_uint64, C.POINTER(tqs_options), fp, u8p]
+            L.tqs_learned_features.restype = st
+            L.tqs_learned_candidate.argtypes = [vp, vp, C.c_uint64, C.POINTER(tqs_options), C.c_uint32, u32p, u64p,
+                                                u32p]
+            L.tqs_learned_candidate.restype = st
+            L.tqs_learned_train.argtypes = [fp, i32p, C.c_size_t, C.c_uint32, C.c_uint32, C.c_float, C.c_uint64, fp,
+                                            fp, fp]
+            L.tqs_learned_train.restype = st
+            L.tqs_learned_loss_grad.argtypes = [fp, fp, i32p, C.c_size_t, fp, fp]
+            L.tqs_learned_loss_grad.restype = st
+            L.tqs_learned_predict.argtypes = [fp, fp, C.c_size_t, fp]
+            L.tqs_learned_predict.restype = st
+            L.tqs_learned_set_model.argtypes = [fp]
+            L.tqs_learned_set_model.restype = st
             L.tqs_last_error.restype = C.c_char_p
             L.tqs_abi_version.restype = C.c_int
             _lib = L
@@ -366,3 +386,68 @@ def tqs_batch_size(b: Batch) -> int:
 
 def tqs_batch_destroy(b: Batch) -> None:
     b.close()
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def tqs_learned_param_count() -> int:
+    return int(lib().tqs_learned_param_count())
+
+
+def tqs_learned_features(c: Handle, nz: Handle, shots: int, opts: Optional[tqs_options] = None):
+    """(features float32[40], allowed uint8[20])."""
+    f = np.zeros(TQS_LEARNED_FEATURES, dtype=np.float32)
+    a = np.zeros(TQS_LEARNED_CLASSES, dtype=np.uint8)
+    _check(lib().tqs_learned_features(c.ptr, nz.ptr, int(shots), C.byref(opts) if opts else None, _fp(f),
+                                      a.ctypes.data_as(C.POINTER(C.c_uint8))))
+    return f, a
+
+
+def tqs_learned_candidate(c: Handle, nz: Handle, shots: int, opts: Optional[tqs_options], cls: int):
+    L = C.c_uint32()
+    a = (C.c_uint64 * TQS_MAX_LEVELS)()
+    s = (C.c_uint32 * (TQS_MAX_LEVELS + 1))()
+    _check(lib().tqs_learned_candidate(c.ptr, nz.ptr, int(shots), C.byref(opts) if opts else None, int(cls),
+                                       C.byref(L), a, s))
+    return list(a[:L.value]), list(s[:L.value + 1])
+
+
+def tqs_learned_train(X, y, epochs: int, batch: int, lr: float, seed: int, init=None):
+    X, y = _f32(X), np.ascontiguousarray(y, dtype=np.int32)
+    w = np.zeros(tqs_learned_param_count(), dtype=np.float32)
+    loss = C.c_float()
+    ini = _f32(init) if init is not None else None
+    _check(lib().tqs_learned_train(_fp(X), y.ctypes.data_as(C.POINTER(C.c_int32)), len(y), int(epochs), int(batch),
+                                   float(lr), int(seed), _fp(ini) if ini is not None else None, _fp(w),
+                                   C.byref(loss)))
+    return w, float(loss.value)
+
+
+def tqs_learned_loss_grad(w, X, y):
+    w, X, y = _f32(w), _f32(X), np.ascontiguousarray(y, dtype=np.int32)
+    g = np.zeros(tqs_learned_param_count(), dtype=np.float32)
+    loss = C.c_float()
+    _check(lib().tqs_learned_loss_grad(_fp(w), _fp(X), y.ctypes.data_as(C.POINTER(C.c_int32)), len(y),
+                                       C.byref(loss), _fp(g)))
+    return float(loss.value), g
+
+
+def tqs_learned_predict(w, X):
+    w, X = _f32(w), _f32(X)
+    out = np.zeros((X.shape[0], TQS_LEARNED_CLASSES), dtype=np.float32)
+    _check(lib().tqs_learned_predict(_fp(w), _fp(X), X.shape[0], _fp(out)))
+    return out
+
+
+def tqs_learned_set_model(w) -> None:
+    if w is None:
+        _check(lib().tqs_learned_set_model(None))
+    else:
+        w = _f32(w)
+        _check(lib().tqs_learned_set_model(_fp(w)))

@@ -9,6 +9,7 @@
 #include <string>
 
 #include "internal.h"
+#include "mlp.h"
 
 namespace tqs {
 
@@ -181,6 +182,25 @@ static std::string dcp(const Circuit &c, const Noise &nz, uint64_t N, double z, 
     return "";
 }
 
+uint64_t dcp_first_arity(const Circuit &c, const Noise &nz, uint64_t N, double z, double eps, uint32_t K)
+{
+    const uint32_t G = (uint32_t)c.gates.size();
+    uint32_t first = G ? (G + K) / (K + 1) : 0;
+    double prod = 1.0;
+    for (uint32_t i = 0; i < first; i++)
+        prod *= (1.0 - (is_two_qubit(c.gates[i].kind) ? nz.p2 : nz.p1));
+    double ph = 1.0 - prod;
+    double n0 = z * z * ph * (1.0 - ph) / (eps * eps);
+    double a = std::ceil(n0 / (1.0 + n0 / (double)N));
+    return a < 1.0 ? 1 : (uint64_t)a;
+}
+
+std::string dcp_tree(const Circuit &c, const Noise &nz, uint64_t N, double z, double eps, uint32_t cgates,
+                     std::vector<uint64_t> &arity, std::vector<uint32_t> &split)
+{
+    return dcp(c, nz, N, z, eps, cgates, arity, split);
+}
+
 std::string partition(const Circuit &c, const Noise &nz, uint64_t N, const tqs_options &o,
                       std::vector<uint64_t> &arity, std::vector<uint32_t> &split)
 {
@@ -248,7 +268,7 @@ std::string partition(const Circuit &c, const Noise &nz, uint64_t N, const tqs_o
         return "";
     }
     case TQS_PART_LEARNED:
-        return "UNSUPPORTED:the learned partitioner is not available in this build";
+        return learned_partition(c, nz, N, o, arity, split);
     default:
         return "unknown partitioner";
     }
@@ -458,6 +478,23 @@ static void compile_programs(PlanHost &P)
         ps.chunk_end = (uint32_t)P.chunk_off.size();
     }
     P.chunk_off.push_back((uint32_t)out.size());
+}
+
+std::vector<uint32_t> pass_starts_one_level(const Circuit &c, uint32_t tile_max)
+{
+    PlanHost P;
+    tqs_options o;
+    tqs_options_default(&o);
+    o.tile_qubits = tile_max;
+    Noise nz = {0, 0, 0};
+    std::vector<uint64_t> arity = {1};
+    std::vector<uint32_t> split = {0, (uint32_t)c.gates.size()};
+    std::vector<uint32_t> starts;
+    if (!build_plan(c, nz, 1, o, arity, split, P).empty())
+        return starts;
+    for (const Pass &ps : P.passes)
+        starts.push_back(ps.site_begin);
+    return starts;
 }
 
 std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const tqs_options &o,
