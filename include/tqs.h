@@ -102,7 +102,12 @@ typedef enum {
 
 #define TQS_FLAG_NO_FIDELITY 0x1u /* skip the ideal run and the fidelity (fidelity = NaN) */
 #define TQS_FLAG_PROFILE 0x2u     /* time every launch with CUDA events (report.prof_*) */
-#define TQS_FLAG_AUTOTUNE 0x4u    /* choose tile_qubits by timing trial runs (cached per circuit shape) */
+#define TQS_FLAG_AUTOTUNE 0x4u    /* choose tile_qubits (and, for FP32, fusion) by timing trial runs,
+                                     cached per circuit shape */
+#define TQS_FLAG_FUSE 0x8u        /* FP32, tiles of 2^11 / 2^12: apply each block of >= 2 consecutive dense
+                                     gates on t - 7 tile qubits as one fused 3xTF32 product on the tensor
+                                     cores (off by default: on circuits whose blocks hold only a few gates
+                                     the per-gate path is faster) */
 
 /* Kernel classes timed under TQS_FLAG_PROFILE (index into report.prof_*). */
 #define TQS_PROF_NOISE 0   /* Philox noise draws + Pauli frames */
@@ -163,6 +168,9 @@ typedef struct {
     uint64_t prof_launches[TQS_PROF_KINDS];
     double prof_ms[TQS_PROF_KINDS];
     double prof_bytes[TQS_PROF_KINDS];
+    /* gate blocks per node per level applied as one fused 2^k x 2^k product on
+     * the tensor cores (FP32 only; 0 when the per-gate path is used) */
+    uint32_t fused_blocks[TQS_MAX_LEVELS];
 } tqs_report;
 
 /* Partition only (host, no GPU): the tree the options select for `shots`.

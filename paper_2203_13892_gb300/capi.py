@@ -23,6 +23,7 @@ TQS_PART_DCP, TQS_PART_UCP, TQS_PART_XCP, TQS_PART_EXPLICIT, TQS_PART_LEARNED = 
 TQS_FLAG_NO_FIDELITY = 0x1
 TQS_FLAG_PROFILE = 0x2
 TQS_FLAG_AUTOTUNE = 0x4
+TQS_FLAG_FUSE = 0x8
 TQS_MAX_LEVELS = 17
 TQS_PROF_KINDS = 4
 PROF_NAMES = ("noise", "store", "sums", "sample")
@@ -61,7 +62,8 @@ class tqs_report(C.Structure):
                 ("kernel_launches", C.c_uint64), ("kernel_ms", C.c_double), ("shots_per_s", C.c_double),
                 ("alg_bytes", C.c_double), ("fid_norm", C.c_double), ("fid_s", C.c_double),
                 ("theo_speedup", C.c_double), ("prof_launches", C.c_uint64 * TQS_PROF_KINDS),
-                ("prof_ms", C.c_double * TQS_PROF_KINDS), ("prof_bytes", C.c_double * TQS_PROF_KINDS)]
+                ("prof_ms", C.c_double * TQS_PROF_KINDS), ("prof_bytes", C.c_double * TQS_PROF_KINDS),
+                ("fused_blocks", C.c_uint32 * TQS_MAX_LEVELS)]
 
     def as_dict(self) -> dict:
         L = self.levels
@@ -69,6 +71,7 @@ class tqs_report(C.Structure):
             "shots_done": self.shots_done, "levels": L,
             "arity": list(self.arity[:L]), "split": list(self.split[:L + 1]),
             "node_instances": list(self.node_instances[:L]), "passes": list(self.passes[:L]),
+            "fused_blocks": list(self.fused_blocks[:L]),
             "kernel_launches": self.kernel_launches, "kernel_ms": self.kernel_ms,
             "shots_per_s": self.shots_per_s, "alg_bytes": self.alg_bytes,
             "fid_norm": self.fid_norm, "fid_s": self.fid_s, "theo_speedup": self.theo_speedup,

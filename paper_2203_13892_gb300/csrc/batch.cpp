@@ -64,6 +64,7 @@ uint64_t shape_key(const tqs_circuit *c, const tqs_options &o, uint64_t shots)
     mix((uint64_t)o.prec);
     mix((uint64_t)o.mode);
     mix((uint64_t)o.part);
+    mix((uint64_t)(o.flags & TQS_FLAG_FUSE));
     mix((uint64_t)(std::log2((double)shots) * 4));
     for (const auto &g : c->c.gates) {
         mix(g.kind);
@@ -74,8 +75,10 @@ uint64_t shape_key(const tqs_circuit *c, const tqs_options &o, uint64_t shots)
 }
 }  // namespace
 
-// Picks tile_qubits for this circuit shape: each candidate width runs the same
-// tree on a few whole level-0 subtrees and the fastest per leaf wins.
+// Picks tile_qubits (and, for FP32, whether dense blocks are fused onto the
+// tensor cores) for this circuit shape: each candidate runs the same tree on a
+// few whole level-0 subtrees and the fastest per leaf wins.  The cache holds
+// tile_qubits | (fuse << 8); a caller that set TQS_FLAG_FUSE keeps it.
 tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options &o,
                     tqs_options &tuned)
 {
@@ -83,11 +86,16 @@ tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, c
     if (o.tile_qubits)
         return TQS_OK;  // the caller fixed it
     const uint64_t key = shape_key(c, o, shots);
+    auto apply = [&](uint32_t v) {
+        tuned.tile_qubits = v & 0xffu;
+        if (v >> 8)
+            tuned.flags |= TQS_FLAG_FUSE;
+    };
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            tuned.tile_qubits = it->second;
+            apply(it->second);
             return TQS_OK;
         }
     }
@@ -103,12 +111,22 @@ tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, c
     const uint64_t trial_roots = std::min<uint64_t>(roots, std::max<uint64_t>(1, 4096 / below));
     const uint64_t trial_shots = std::min<uint64_t>(shots, trial_roots * below);
     const uint32_t n = c->c.n;
-    std::vector<uint32_t> cands = o.prec == TQS_FP64 ? std::vector<uint32_t>{9, 10, 11, 12}
-                                                     : std::vector<uint32_t>{10, 11, 12, 13};
+    const bool may_fuse = o.prec == TQS_FP32 && !(o.flags & TQS_FLAG_FUSE);
+    std::vector<uint32_t> cands;  // tile_qubits | (fuse << 8)
+    if (o.prec == TQS_FP64)
+        cands = {9, 10, 11, 12};
+    else
+        cands = {10, 11, 12, 13};
+    if (may_fuse)
+        for (uint32_t t : {11u, 12u})
+            if (t <= n)
+                cands.push_back(t | 0x100u);
+    const uint32_t fuse_all = (o.flags & TQS_FLAG_FUSE) ? 0x100u : 0u;
     uint32_t best = 0;
     double best_t = 1e300;
     bool small_done = false;
-    for (uint32_t t : cands) {
+    for (uint32_t cand : cands) {
+        const uint32_t t = cand & 0xffu;
         if (t > n) {  // every width >= n gives the same single-tile plan
             if (small_done)
                 continue;
@@ -116,6 +134,8 @@ tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, c
         }
         tqs_options tr = o;
         tr.flags &= ~(TQS_FLAG_AUTOTUNE | TQS_FLAG_PROFILE);
+        if (cand >> 8)
+            tr.flags |= TQS_FLAG_FUSE;
         tr.part = TQS_PART_EXPLICIT;
         tr.k = (uint32_t)arity.size() - 1;
         tr.arity = arity.data();
@@ -141,14 +161,14 @@ tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, c
         }
         if (ms < best_t) {
             best_t = ms;
-            best = t;
+            best = cand | fuse_all;
         }
     }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
     }
-    tuned.tile_qubits = best;
+    apply(best);
     return TQS_OK;
 }
 
@@ -276,6 +296,12 @@ tqs_status tqs_batch_execute(tqs_batch *b, const uint64_t *seeds, tqs_report *re
         e = cudaStreamSynchronize(b->origin);
     if (e != cudaSuccess)
         return fail_cuda("tqs_batch_execute", e);
+    for (auto &p : b->plans) {
+        std::string err;
+        const tqs_status st = p->dp.check_device_error(err);
+        if (st != TQS_OK)
+            return tqs::set_error(st, err);
+    }
     if (report) {
         float ms = 0;
         cudaEventElapsedTime(&ms, b->ev0, b->ev1);

@@ -80,6 +80,8 @@ void fill_report(const tqs_plan *p, double ms, tqs_report *r)
         r->split[i] = H.levels[i].g0;
         r->node_instances[i] = i < p->dp.node_count.size() ? p->dp.node_count[i] : 0;
         r->passes[i] = H.levels[i].pass_end - H.levels[i].pass_begin;
+        for (uint32_t q = H.levels[i].pass_begin; q < H.levels[i].pass_end; q++)
+            r->fused_blocks[i] += H.passes[q].fused_blocks;
         inst += (double)r->node_instances[i];
     }
     r->split[r->levels] = H.levels.back().g1;
@@ -248,6 +250,9 @@ tqs_status tqs_plan_execute(tqs_plan *p, uint64_t seed, uint64_t *d_counts, tqs_
     if (st != TQS_OK)
         return fail(st, err);
     if (report) {
+        st = p->dp.check_device_error(err);
+        if (st != TQS_OK)
+            return fail(st, err);
         cudaError_t e = cudaEventSynchronize(p->dp.ev1);
         float ms = 0;
         if (e == cudaSuccess)
@@ -272,6 +277,9 @@ tqs_status tqs_simulate(const tqs_circuit *c, const tqs_noise *nz, uint64_t shot
     std::string err;
     cudaStream_t s = p->dp.stream;
     st = p->dp.execute(seed, p->dp.d_counts_internal, true, err);
+    if (st != TQS_OK)
+        return fail(st, err);
+    st = p->dp.check_device_error(err);
     if (st != TQS_OK)
         return fail(st, err);
     const size_t bytes = sizeof(uint64_t) * ((size_t)1 << c->c.n);
@@ -316,6 +324,8 @@ tqs_status tqs_debug_node_state(const tqs_circuit *c, const tqs_noise *nz, uint6
         return fail(TQS_EINVAL, "node is not simulated at this level");
     std::string err;
     st = p->dp.run_chain(level, node, seed, err);
+    if (st == TQS_OK)
+        st = p->dp.check_device_error(err);
     if (st != TQS_OK)
         return fail(st, err);
     const uint64_t dim = (uint64_t)1 << H.n;

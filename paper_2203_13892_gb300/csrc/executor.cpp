@@ -98,6 +98,8 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
     size_t o_mats = take((H.prec == TQS_FP64 ? 8 : 4) * H.mats64.size());
     size_t o_pst = take(sizeof(uint32_t) * (H.passes.size() + L) + 64);
     size_t o_prog = take(std::max<size_t>(H.prog.size(), 16));
+    size_t o_fused = take(sizeof(float) * std::max<size_t>(H.fused.size(), 4));
+    size_t o_err = take(sizeof(unsigned int) * 4);
     size_t o_choff = take(sizeof(uint32_t) * std::max<size_t>(H.chunk_off.size(), 1));
     size_t o_fid = take(sizeof(double) * (3 + 3 * 256));
     size_t o_perm = take(32);
@@ -119,6 +121,8 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
         d_mats = b + o_mats;
         d_pass_start = (uint32_t *)(b + o_pst);
         d_prog = (uint8_t *)(b + o_prog);
+        d_fused = (float *)(b + o_fused);
+        d_err = (unsigned int *)(b + o_err);
         d_chunk_off = (uint32_t *)(b + o_choff);
         d_fid = (double *)(b + o_fid);
         d_perm = (uint8_t *)(b + o_perm);
@@ -199,6 +203,9 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
     CK(cudaMemcpyAsync(d_pass_start, pst_host.data(), 4 * pst_host.size(), cudaMemcpyHostToDevice, stream));
     if (!H.prog.empty())
         CK(cudaMemcpyAsync(d_prog, H.prog.data(), H.prog.size(), cudaMemcpyHostToDevice, stream));
+    if (!H.fused.empty())
+        CK(cudaMemcpyAsync(d_fused, H.fused.data(), 4 * H.fused.size(), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemsetAsync(d_err, 0, 4 * sizeof(unsigned int), stream));
     CK(cudaMemcpyAsync(d_chunk_off, H.chunk_off.data(), 4 * H.chunk_off.size(), cudaMemcpyHostToDevice, stream));
     uint8_t perm[32] = {0};
     for (uint32_t q = 0; q < H.n; q++)
@@ -261,6 +268,9 @@ tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vect
         a.chunk_off = d_chunk_off;
         a.chunk_begin = ps.chunk_begin;
         a.chunk_end = ps.chunk_end;
+        a.fused = ps.fused_blocks ? d_fused : nullptr;
+        a.fused_k = ps.fused_blocks ? H.fused_k : 0;
+        a.err = d_err;
         a.n = H.n;
         a.t = ps.t;
         a.L = ps.L;
@@ -388,6 +398,9 @@ tqs_status DevicePlan::run_chain(uint32_t level, uint64_t node, uint64_t seed, s
             a.chunk_off = d_chunk_off;
             a.chunk_begin = ps.chunk_begin;
             a.chunk_end = ps.chunk_end;
+            a.fused = ps.fused_blocks ? d_fused : nullptr;
+            a.fused_k = ps.fused_blocks ? H.fused_k : 0;
+            a.err = d_err;
             a.n = H.n;
             a.t = ps.t;
             a.L = ps.L;
@@ -402,6 +415,23 @@ tqs_status DevicePlan::run_chain(uint32_t level, uint64_t node, uint64_t seed, s
             a.seed = seed;
             CKL(launch_pass(a, stream));
         }
+    }
+    return TQS_OK;
+}
+
+tqs_status DevicePlan::check_device_error(std::string &err)
+{
+    unsigned int h = 0;
+    CK(cudaMemcpyAsync(&h, d_err, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (h) {
+        CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned int), stream));
+        if (h & 2u) {
+            err = "internal: a fused-gate record reached a kernel built without the tensor-core path";
+            return TQS_ECUDA;
+        }
+        err = "a bounded tensor-core wait gave up (device error word " + std::to_string(h) + ")";
+        return TQS_ETIMEOUT;
     }
     return TQS_OK;
 }

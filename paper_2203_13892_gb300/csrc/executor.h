@@ -26,6 +26,8 @@ struct DevicePlan {
     void *d_mats = nullptr;
     uint32_t *d_pass_start = nullptr;
     uint8_t *d_prog = nullptr;
+    float *d_fused = nullptr;
+    unsigned int *d_err = nullptr;
     uint32_t *d_chunk_off = nullptr;
     double *d_fid = nullptr;
     uint8_t *d_perm = nullptr;
@@ -55,6 +57,8 @@ struct DevicePlan {
     tqs_status run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vector<uint64_t> &plo,
                          uint64_t seed, unsigned long long *counts, std::string &err);
     tqs_status run_chain(uint32_t level, uint64_t node, uint64_t seed, std::string &err);
+    // reads and clears the device error word (synchronises the stream)
+    tqs_status check_device_error(std::string &err);
     bool profiling() const { return (opts.flags & TQS_FLAG_PROFILE) != 0; }
 };
 

@@ -74,7 +74,13 @@ struct Noise {
 // A run's factors: the product over its gates of D = G * prod a_q^{x_q} *
 // prod c_qr^{x_q x_r}, merged per qubit and per pair and classified by where
 // the bits live (thread bit, register slot bit, outside the tile).
-enum RecType : uint8_t { REC_DENSE1 = 1, REC_DENSE2 = 2, REC_RUN = 3 };
+//   REC_FUSED   a=k (fused qubits)      no payload; ibeg/iend = the fused gates; `site` =
+//               their first site; the 16 bytes after the header hold the k tile positions
+//               (bytes 0..7), the k physical bits (bytes 8..15); the following 16 bytes hold
+//               the float offset of the operand in PlanHost::fused (u32) and three zero words.
+//               The kernels apply it as one 2^k x 2^k complex product on the tensor cores
+//               (FP32 states only, k = t - 7 so that a tile has 128 columns).
+enum RecType : uint8_t { REC_DENSE1 = 1, REC_DENSE2 = 2, REC_RUN = 3, REC_FUSED = 4 };
 enum FacKind : uint8_t {
     FAC_A_FIXED = 1,   // a^{x_p}, p a thread bit or outside the tile
     FAC_A_SLOT = 2,    // a^{x}, on slot bit s = j0 - 8
@@ -98,6 +104,7 @@ struct Pass {
     uint32_t level;
     uint32_t ibeg, iend;          // instruction range (global instruction list)
     uint32_t chunk_begin, chunk_end;  // program chunks (offsets in PlanHost::chunk_off)
+    uint32_t fused_blocks;        // REC_FUSED records in the program
     uint32_t site_begin;          // first site of the pass, relative to the level
     uint32_t t, L;                // tile width and number of contiguous low bits
     uint8_t tbits[kMaxTile];      // physical bit of each tile position (ascending)
@@ -137,6 +144,9 @@ struct PlanHost {
     std::vector<float> mats32;     // 32 floats per gate
     std::vector<uint8_t> prog;     // compiled pass programs (state precision), all passes
     std::vector<uint32_t> chunk_off; // chunk boundaries into prog (chunk c = [off[c], off[c+1]))
+    std::vector<float> fused;        // fused-gate operands (TF32 hi/lo, tensor-core B layout)
+    uint32_t fused_k = 0;            // qubits per fused gate in this plan (0: none)
+    bool fuse = false;               // FP32: fuse dense gate blocks onto the tensor cores
     uint64_t thr1, thr2, thrm;     // floor(p * 2^32)
     SamplerLayout samp;
     uint32_t tile_max;
@@ -209,6 +219,9 @@ struct PassLaunch {
     unsigned long long *counts;
     const uint64_t *seed_dev;  // when non-null the seed is read here (graph replays)
     uint64_t seed, thrm;
+    const float *fused;        // fused-gate operands (device), nullptr when the pass has none
+    uint32_t fused_k;          // qubits per fused gate (0: none)
+    unsigned int *err;         // device error word: bit 0 = a bounded tensor-core wait gave up
 };
 int launch_pass(const PassLaunch &a, void *stream);
 // Sets the shared-memory limits of every kernel variant (call before a stream capture).

@@ -145,6 +145,101 @@ int launch_noise(const NoiseLaunch &a, void *stream)
 }
 
 // ---------------------------------------------------------------------------
+// Blackwell tensor-core helpers (tcgen05 / TMEM / mbarrier), used by fused gates
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major operand without swizzle; lbo / sbo are
+// the byte distances between core matrices adjacent in K / in the row dimension.
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of tcgen05.mma .kind::tf32: D F32, A and B TF32, both K-major.
+__host__ __device__ constexpr uint32_t tc_idesc_tf32(uint32_t M, uint32_t N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_alloc(uint32_t slot_saddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_saddr), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar_saddr)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_saddr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar_saddr, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_saddr), "r"(count) : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier: true when it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar_saddr, uint32_t parity, uint32_t max_iter)
+{
+    for (uint32_t it = 0; it < max_iter; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(mbar_saddr), "r"(parity)
+            : "memory");
+        if (ok)
+            return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 lanes x 32 bits x 16 columns from TMEM (this warp's lane quarter).
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&r)[16])
+{
+    uint32_t u[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++)
+        r[i] = __uint_as_float(u[i]);
+}
+
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// ---------------------------------------------------------------------------
 // Pass kernel
 // ---------------------------------------------------------------------------
 struct PassK {
@@ -161,7 +256,10 @@ struct PassK {
     double *S;
     unsigned long long *counts;
     const uint64_t *seed_dev;
+    const float *fused;
+    unsigned int *err;
     uint64_t seed, thrm;
+    uint32_t fused_k;
     uint32_t ibeg, iend, n, t, L, sites, meta_stride, pass_local;
     uint32_t chunk_begin, chunk_end;
     int in_from_parent;
@@ -282,6 +380,7 @@ template <typename C, int NS> struct DiagAcc {
     C E[NS > 0 ? NS : 1];
     C Gs[NS > 1 ? NS * (NS - 1) / 2 : 1];
     bool has_gs;
+    uint32_t e_used;  // slot factors that some gate touched (uniform)
     __device__ __forceinline__ void reset()
     {
         base = mk((decltype(base.x))1, (decltype(base.x))0);
@@ -292,9 +391,11 @@ template <typename C, int NS> struct DiagAcc {
         for (int i = 0; i < (NS > 1 ? NS * (NS - 1) / 2 : 1); i++)
             Gs[i] = base;
         has_gs = false;
+        e_used = 0;
     }
     __device__ __forceinline__ void mul_E(int s, C f)
     {
+        e_used |= 1u << s;
         // s is uniform across the CTA: a branch, not predicated copies
         switch (s) {
         case 0: if (NS > 0) E[0] = cmul(E[0], f); break;
@@ -313,6 +414,7 @@ template <typename C, int NS> struct DiagAcc {
             if (k == idx)
                 Gs[k] = cmul(Gs[k], f);
         has_gs = true;
+        e_used |= (1u << s0) | (1u << s1);
     }
 };
 
@@ -399,11 +501,14 @@ __device__ __forceinline__ void acc_flush(DiagAcc<C, LOGR> &A, C (&v)[1 << LOGR]
     for (int k = 0; k < NR; k++)
         v[k] = cmul(v[k], base);
 #pragma unroll
-    for (int sb = 0; sb < LOGR; sb++)
+    for (int sb = 0; sb < LOGR; sb++) {
+        if (!((A.e_used >> sb) & 1u) && !((msig >> sb) & 1u))
+            continue;  // untouched slot factor: exactly 1
 #pragma unroll
         for (int k = 0; k < NR; k++)
             if ((k >> sb) & 1)
                 v[k] = cmul(v[k], Eb[sb]);
+    }
     if (A.has_gs) {
 #pragma unroll
         for (int hi = 1; hi < LOGR; hi++)
@@ -464,7 +569,10 @@ template <typename C> __device__ __forceinline__ C shfl_xor_c(C a, int m)
 #ifndef TQS_FP32_MIN_CTAS
 #define TQS_FP32_MIN_CTAS 2  // resident CTAs per SM asked of ptxas for FP32 tiles of 2^12 amplitudes
 #endif
-template <typename R, int MODE, int LOGR>
+// FUSE: the pass holds REC_FUSED records (FP32 tiles of 2^11 or 2^12 only); a
+// separate instantiation so that the tensor-core code does not weigh on the
+// register allocation of the passes without fused gates.
+template <typename R, int MODE, int LOGR, bool FUSE>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP32_MIN_CTAS : (LOGR == 3 ? 3 : 4))
                                                            : (LOGR >= 3 ? 1 : 2))
     pass_kernel(const __grid_constant__ PassK a)
@@ -512,6 +620,27 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                     e |= 1u << SL.rank_pos[rb + b];
             lut[i] = (uint16_t)e;
         }
+    }
+
+    // ---- tensor-core resources of fused gates (FP32 passes that have them) --
+    const uint32_t nzst_k = ((a.sites < (uint32_t)kNoiseStage ? a.sites : (uint32_t)kNoiseStage) + 15u) / 16u * 16u;
+    unsigned char *fz = nullptr;
+    uint32_t tc_cols = 0, tc_phase = 0;
+    if (FUSE && a.fused_k) {
+        const size_t te_b = (size_t)(TE < (uint32_t)kThreads ? (uint32_t)kThreads : TE) * sizeof(C);
+        size_t off = te_b + 256 * 2 + kThreads * 8 + 4 * 8 + 32 * 4 + nzst_k + kProgChunkBytes;
+        off = (off + 127) / 128 * 128;
+        fz = smem + off;
+        const uint32_t K = 2u << a.fused_k;
+        unsigned char *tail = fz + te_b + 2 * (size_t)K * K * 4;  // mbarrier (8 B), TMEM slot (4 B)
+        tc_cols = K < 32u ? 32u : K;
+        if (tid < 32)
+            tc_alloc(smem_u32(tail + 8), tc_cols);
+        if (tid == 0) {
+            mbar_init(smem_u32(tail), 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        tc_fence_before();
     }
 
     // ---- which tile ------------------------------------------------------
@@ -740,6 +869,126 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
         }
         pending = true;
     };
+    // One fused gate on the tensor cores: the tile seen as a 2^kf x 128 complex
+    // matrix X (rows: the fused qubits' local index, columns: the other tile
+    // bits), Y = U X computed as the real product [Yr; Yi]^T = [Xr; Xi]^T [[Ur,-Ui],[Ui,Ur]]^T
+    // (M = 128 columns, N = K = 2^(kf+1)) in three TF32 products
+    // (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM).
+    auto fused_apply = [&](const unsigned char *pay, uint32_t kf) {
+        if constexpr (sizeof(R) == 4 && FUSE) {
+            const uint32_t Kc = 1u << kf, Kr = 2u * Kc;
+            uint32_t jpos[5], phys[5];
+            uint32_t jmask = 0, mu = 0;
+            for (uint32_t i = 0; i < kf; i++) {
+                jpos[i] = pay[i];
+                phys[i] = pay[8 + i];
+                jmask |= 1u << jpos[i];
+                mu |= ((mask >> phys[i]) & 1u) << i;
+            }
+            const uint32_t foff = *reinterpret_cast<const uint32_t *>(pay + 16);
+            const size_t te_b = (size_t)TE * sizeof(C);
+            float *A_hi = reinterpret_cast<float *>(s);
+            float *A_lo = reinterpret_cast<float *>(fz);
+            float *B_hi = reinterpret_cast<float *>(fz + te_b);
+            float *B_lo = B_hi + (size_t)Kr * Kr;
+            const uint32_t mbar = smem_u32(B_lo + (size_t)Kr * Kr);
+            const uint32_t tmem = *reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(B_lo + (size_t)Kr * Kr) + 8);
+            // split of a tile position set: fused bits -> local index, the rest -> column
+            auto gather = [&](uint32_t e) {
+                uint32_t r = 0;
+                for (uint32_t i = 0; i < kf; i++)
+                    r |= ((e >> jpos[i]) & 1u) << i;
+                return r;
+            };
+            auto compress = [&](uint32_t e) {
+                uint32_t r = 0, o = 0;
+                for (uint32_t j = 0; j < a.t; j++)
+                    if (!((jmask >> j) & 1u))
+                        r |= ((e >> j) & 1u) << (o++);
+                return r;
+            };
+            auto offA = [&](uint32_t c, uint32_t kk) {
+                return (c >> 3) * (Kr / 4) * 32 + (kk >> 2) * 32 + (c & 7u) * 4 + (kk & 3u);
+            };
+            __syncthreads();  // the tile region is free (all earlier exchanges finished)
+            {
+                const float4 *src = reinterpret_cast<const float4 *>(a.fused + foff);
+                float4 *dst = reinterpret_cast<float4 *>(B_hi);
+                for (uint32_t x = tid; x < Kr * Kr / 2; x += kThreads)  // hi and lo, 4 floats each
+                    dst[x] = src[x];
+            }
+            const uint32_t at = gather(tid), ct = compress(tid);
+#pragma unroll
+            for (int k = 0; k < NR; k++) {
+                const uint32_t ek = (uint32_t)k * kThreads;
+                const uint32_t aa = (at | gather(ek)) ^ mu, cc = ct | compress(ek);
+                const float re = v[k].x, im = v[k].y;
+                const float hr = tf32_rna(re), hm = tf32_rna(im);
+                A_hi[offA(cc, aa)] = hr;
+                A_lo[offA(cc, aa)] = tf32_rna(re - hr);
+                A_hi[offA(cc, Kc + aa)] = hm;
+                A_lo[offA(cc, Kc + aa)] = tf32_rna(im - hm);
+            }
+            fence_async_smem();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                const uint32_t idesc = tc_idesc_tf32(128, Kr);
+                const uint32_t sbo = Kr / 4 * 128;
+                const uint32_t sa[3] = {smem_u32(A_hi), smem_u32(A_hi), smem_u32(A_lo)};
+                const uint32_t sb[3] = {smem_u32(B_hi), smem_u32(B_lo), smem_u32(B_hi)};
+                for (uint32_t term = 0; term < 3; term++)
+                    for (uint32_t ks = 0; ks < Kr / 8; ks++)
+                        tc_mma_tf32(tmem, tc_smem_desc(sa[term] + ks * 256, 128, sbo),
+                                    tc_smem_desc(sb[term] + ks * 256, 128, sbo), idesc, (term | ks) != 0);
+                tc_commit(mbar);
+            }
+            const bool ok = mbar_wait_bounded(mbar, tc_phase, 1u << 22);
+            tc_phase ^= 1u;
+            tc_fence_after();
+            __syncthreads();
+            if (!ok) {
+                if (tid == 0 && a.err)
+                    atomicOr(a.err, 1u);
+                // give the products in flight a second bounded chance before TMEM is reused
+                mbar_wait_bounded(mbar, tc_phase ^ 1u, 1u << 22);
+                __syncthreads();
+                return;  // results of this block are not applied; the host reports TQS_ETIMEOUT
+            }
+            // D[c][o] from TMEM: warp w reads rows 32*(w%4)..+31 (its lane quarter) and
+            // one half of the Kr columns
+            const uint32_t w = tid >> 5, lane = tid & 31u;
+            const uint32_t c = 32u * (w & 3u) + lane;
+            float *sf = reinterpret_cast<float *>(s);
+            uint32_t dc = 0;  // tile positions of column c
+            {
+                uint32_t o = 0;
+                for (uint32_t j = 0; j < a.t; j++)
+                    if (!((jmask >> j) & 1u))
+                        dc |= ((c >> (o++)) & 1u) << j;
+            }
+            const uint32_t half = Kr / 2, col0 = (w >> 2) * half;
+            for (uint32_t cb = 0; cb < half; cb += 16) {
+                float r[16];
+                tc_ld16(tmem + ((32u * (w & 3u)) << 16) + col0 + cb, r);
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const uint32_t o = col0 + cb + (uint32_t)i;
+                    const uint32_t ast = (o & (Kc - 1u)) ^ mu;
+                    uint32_t e = dc;
+                    for (uint32_t b = 0; b < kf; b++)
+                        e |= ((ast >> b) & 1u) << jpos[b];
+                    sf[2 * e + (o >= Kc ? 1 : 0)] = r[i];
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                v[k] = s[tid + k * kThreads];
+            __syncthreads();
+        }
+    };
     constexpr uint32_t CS = (uint32_t)sizeof(C);
     if (!zero_tile) {
         for (uint32_t c = a.chunk_begin; c < a.chunk_end; c++) {
@@ -771,6 +1020,41 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                     if (pz)
                         apply_noise(pz, 15, ha, hc, hb, hd);
                     p += 16u + 16u * CS;
+                } else if (htype == REC_FUSED) {
+                  if constexpr (!FUSE) {  // the host launches the FUSE instantiation for these
+                    if (tid == 0 && a.err)
+                        atomicOr(a.err, 2u);
+                  } else {
+                    const uint32_t nsites = hiend - hibeg;
+                    uint32_t any = 0;
+                    for (uint32_t x = 0; x < nsites; x++)
+                        any |= noise_at(hsite + x);
+                    bool done = false;
+                    if constexpr (sizeof(R) == 4) {
+                        if (!any && a.fused_k == ha) {
+                            flush();
+                            fused_apply(pay, ha);
+                            done = true;
+                        }
+                    }
+                    if (!done) {  // a noise site inside the block: the gates one by one
+                        for (uint32_t ii = hibeg; ii < hiend; ii++) {
+                            const Instr I = a.instr[ii];
+                            const R *M = mats + (size_t)I.gate * 32;
+                            if (I.op == OP_DENSE1) {
+                                dense1(I.j0, I.p0, mk(M[0], M[1]), mk(M[2], M[3]), mk(M[4], M[5]), mk(M[6], M[7]));
+                            } else if (I.op == OP_DENSE2) {
+                                dense2(I.j0, I.j1, I.p0, I.p1, [&](uint32_t kk) { return mk(M[2 * kk], M[2 * kk + 1]); });
+                            } else if (I.op == OP_DIAG1 || I.op == OP_DIAG2) {
+                                diag_gate(I);
+                            }
+                            const uint32_t pz = noise_at(I.site);
+                            if (pz)
+                                apply_noise(pz, I.npaulis, I.j0, I.np0, I.j1, I.np1);
+                        }
+                    }
+                  }
+                    p += 48u;
                 } else {
                     const uint32_t nfac = ha + hb + hc + hd + he;
                     const uint32_t nsites = hiend - hibeg;
@@ -826,6 +1110,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
         flush();
     } else {
         mask = m1.mask;
+    }
+    if (FUSE && a.fused_k) {  // every path reaches here: free the tensor memory
+        tc_fence_before();
+        __syncthreads();
+        if (tid < 32) {
+            const uint32_t K = 2u << a.fused_k;
+            const uint32_t tmem = *reinterpret_cast<const uint32_t *>(fz + (size_t)TE * sizeof(C) + 2 * (size_t)K * K * 4 + 8);
+            tc_dealloc(tmem, tc_cols);
+        }
     }
 
     // ---- epilogue ------------------------------------------------------
@@ -946,32 +1239,36 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     }
 }
 
-template <typename R, int MODE, int LOGR> static int set_pass_attr()
+template <typename R, int MODE, int LOGR, bool FUSE> static int set_pass_attr()
 {
-    return (int)cudaFuncSetAttribute(pass_kernel<R, MODE, LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return (int)cudaFuncSetAttribute(pass_kernel<R, MODE, LOGR, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      200 * 1024);
 }
 
-template <typename R, int MODE, int LOGR>
+template <typename R, int MODE, int LOGR, bool FUSE>
 static int launch_pass_t(const PassK &k, dim3 grid, size_t smem, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        set_pass_attr<R, MODE, LOGR>();
+        set_pass_attr<R, MODE, LOGR, FUSE>();
         attr = true;
     }
-    pass_kernel<R, MODE, LOGR><<<grid, kThreads, smem, st>>>(k);
+    pass_kernel<R, MODE, LOGR, FUSE><<<grid, kThreads, smem, st>>>(k);
     return (int)cudaGetLastError();
 }
 
 template <typename R, int MODE> static int set_attrs_r()
 {
-    int e = set_pass_attr<R, MODE, 0>();
-    e |= set_pass_attr<R, MODE, 1>();
-    e |= set_pass_attr<R, MODE, 2>();
-    e |= set_pass_attr<R, MODE, 3>();
-    e |= set_pass_attr<R, MODE, 4>();
-    e |= set_pass_attr<R, MODE, 5>();
+    int e = set_pass_attr<R, MODE, 0, false>();
+    e |= set_pass_attr<R, MODE, 1, false>();
+    e |= set_pass_attr<R, MODE, 2, false>();
+    e |= set_pass_attr<R, MODE, 3, false>();
+    e |= set_pass_attr<R, MODE, 4, false>();
+    e |= set_pass_attr<R, MODE, 5, false>();
+    if (sizeof(R) == 4) {
+        e |= set_pass_attr<R, MODE, 3, true>();
+        e |= set_pass_attr<R, MODE, 4, true>();
+    }
     return e;
 }
 
@@ -985,13 +1282,18 @@ int prepare_kernels()
 template <typename R, int MODE>
 static int launch_pass_r(const PassK &k, int logr, dim3 grid, size_t smem, cudaStream_t st)
 {
+    if (sizeof(R) == 4 && k.fused_k) {  // the planner fuses only in tiles of 2^11 and 2^12
+        if (logr == 3) return launch_pass_t<R, MODE, 3, true>(k, grid, smem, st);
+        if (logr == 4) return launch_pass_t<R, MODE, 4, true>(k, grid, smem, st);
+        return (int)cudaErrorInvalidValue;
+    }
     switch (logr) {
-    case 0: return launch_pass_t<R, MODE, 0>(k, grid, smem, st);
-    case 1: return launch_pass_t<R, MODE, 1>(k, grid, smem, st);
-    case 2: return launch_pass_t<R, MODE, 2>(k, grid, smem, st);
-    case 3: return launch_pass_t<R, MODE, 3>(k, grid, smem, st);
-    case 4: return launch_pass_t<R, MODE, 4>(k, grid, smem, st);
-    default: return launch_pass_t<R, MODE, 5>(k, grid, smem, st);
+    case 0: return launch_pass_t<R, MODE, 0, false>(k, grid, smem, st);
+    case 1: return launch_pass_t<R, MODE, 1, false>(k, grid, smem, st);
+    case 2: return launch_pass_t<R, MODE, 2, false>(k, grid, smem, st);
+    case 3: return launch_pass_t<R, MODE, 3, false>(k, grid, smem, st);
+    case 4: return launch_pass_t<R, MODE, 4, false>(k, grid, smem, st);
+    default: return launch_pass_t<R, MODE, 5, false>(k, grid, smem, st);
     }
 }
 
@@ -1018,6 +1320,9 @@ int launch_pass(const PassLaunch &a, void *stream)
     k.counts = a.counts;
     k.seed = a.seed;
     k.seed_dev = a.seed_dev;
+    k.fused = a.fused;
+    k.fused_k = a.fused ? a.fused_k : 0;
+    k.err = a.err;
     k.thrm = a.thrm;
     k.ibeg = a.ibeg;
     k.iend = a.iend;
@@ -1039,7 +1344,11 @@ int launch_pass(const PassLaunch &a, void *stream)
     const size_t elem = a.fp64 ? 16 : 8;
     const size_t te = ((size_t)1 << a.t) < (size_t)kThreads ? (size_t)kThreads : ((size_t)1 << a.t);
     const size_t nzst = ((a.sites < (uint32_t)kNoiseStage ? a.sites : (uint32_t)kNoiseStage) + 15u) / 16u * 16u;
-    const size_t smem = te * elem + 256 * 2 + kThreads * 8 + 4 * 8 + 32 * 4 + nzst + kProgChunkBytes;
+    size_t smem = te * elem + 256 * 2 + kThreads * 8 + 4 * 8 + 32 * 4 + nzst + kProgChunkBytes;
+    if (k.fused_k) {  // A lo (the tile region doubles as A hi), B hi/lo, mbarrier and TMEM slot
+        const size_t K = (size_t)2 << k.fused_k;
+        smem = (smem + 127) / 128 * 128 + te * elem + 2 * K * K * 4 + 128;
+    }
     const int logr = a.t > 8 ? (int)a.t - 8 : 0;
     const uint64_t tiles = (uint64_t)1 << (a.n - a.t);
     dim3 grid = a.mode == MODE_SAMPLE ? dim3(a.nnodes) : dim3((unsigned)tiles, a.nnodes);

@@ -48,8 +48,9 @@ std::vector<uint32_t> equal_cuts(uint32_t G, uint32_t L)
 }
 }  // namespace
 
-std::string learned_candidate(const Circuit &c, const Noise &nz, uint64_t N, const tqs_options &o, uint32_t cls,
-                              std::vector<uint64_t> &arity, std::vector<uint32_t> &split)
+static std::string candidate_impl(const Circuit &c, const Noise &nz, uint64_t N, const tqs_options &o, uint32_t cls,
+                                  const std::vector<uint32_t> *starts_in, std::vector<uint64_t> &arity,
+                                  std::vector<uint32_t> &split)
 {
     if (cls >= (uint32_t)kMlpClasses)
         return "class out of range";
@@ -75,8 +76,12 @@ std::string learned_candidate(const Circuit &c, const Noise &nz, uint64_t N, con
     arity[0] = (uint64_t)(((unsigned __int128)N + pk - 1) / pk);
     split = equal_cuts(G, k + 1);
     if (mode == 1) {
-        const uint32_t t = o.tile_qubits ? o.tile_qubits : (o.prec == TQS_FP64 ? 11 : 12);
-        std::vector<uint32_t> starts = pass_starts_one_level(c, t);
+        std::vector<uint32_t> own;
+        if (!starts_in) {
+            const uint32_t t = o.tile_qubits ? o.tile_qubits : (o.prec == TQS_FP64 ? 11 : 12);
+            own = pass_starts_one_level(c, t);
+        }
+        const std::vector<uint32_t> &starts = starts_in ? *starts_in : own;
         for (uint32_t i = 1; i <= k; i++) {
             uint32_t best = split[i], bd = 0xffffffffu;
             for (uint32_t s : starts) {
@@ -96,6 +101,12 @@ std::string learned_candidate(const Circuit &c, const Noise &nz, uint64_t N, con
                 return "invalid: aligned cuts collide";
     }
     return "";
+}
+
+std::string learned_candidate(const Circuit &c, const Noise &nz, uint64_t N, const tqs_options &o, uint32_t cls,
+                              std::vector<uint64_t> &arity, std::vector<uint32_t> &split)
+{
+    return candidate_impl(c, nz, N, o, cls, nullptr, arity, split);
 }
 
 std::string learned_features(const Circuit &c, const Noise &nz, uint64_t N, const tqs_options &o, float *f,
@@ -129,13 +140,14 @@ std::string learned_features(const Circuit &c, const Noise &nz, uint64_t N, cons
     }
     f[38] = G ? (float)dense / (float)G : 0.f;
     const uint32_t t = o.tile_qubits ? o.tile_qubits : (o.prec == TQS_FP64 ? 11 : 12);
-    f[39] = (float)pass_starts_one_level(c, t).size() / 64.f;
+    const std::vector<uint32_t> starts = pass_starts_one_level(c, t);
+    f[39] = (float)starts.size() / 64.f;
     if (allowed) {
         for (uint32_t cls = 0; cls < (uint32_t)kMlpClasses; cls++) {
             std::vector<uint64_t> a;
             std::vector<uint32_t> s;
             allowed[cls] = 0;
-            if (!learned_candidate(c, nz, N, o, cls, a, s).empty())
+            if (!candidate_impl(c, nz, N, o, cls, &starts, a, s).empty())
                 continue;
             const uint32_t k = cls % 10;
             if (k > kd)

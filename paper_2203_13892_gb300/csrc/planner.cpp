@@ -303,10 +303,107 @@ static void choose_tile(uint32_t n, uint32_t tmax, uint32_t need_mask, const uin
     p.L = L;
 }
 
+// TF32 rounding (nearest, ties to even on the 10-bit mantissa) of an FP32 value.
+static float tf32_round(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u)
+        u = (u + 0x0fffu + ((u >> 13) & 1u)) & 0xffffe000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+// Dense 2^k x 2^k unitary of a block of gates on the physical bits q[0..k-1]
+// (local index bit i <-> q[i]), FP64, row-major.
+static std::vector<std::complex<double>> fused_unitary(const PlanHost &P, const std::vector<uint32_t> &ids,
+                                                       const uint8_t *q, uint32_t k)
+{
+    const uint32_t d = 1u << k;
+    std::vector<std::complex<double>> U(d * d, 0.0), T(d * d);
+    for (uint32_t i = 0; i < d; i++)
+        U[i * d + i] = 1.0;
+    auto loc = [&](uint8_t p) {
+        for (uint32_t i = 0; i < k; i++)
+            if (q[i] == p)
+                return i;
+        return 0u;
+    };
+    for (uint32_t id : ids) {
+        const Instr &in = P.instrs[id];
+        if (in.op == OP_NOP)
+            continue;
+        const double *m = &P.mats64[(size_t)in.gate * 32];
+        auto cx = [&](int e) { return std::complex<double>(m[2 * e], m[2 * e + 1]); };
+        const bool two = in.op == OP_DENSE2 || in.op == OP_DIAG2;
+        const uint32_t l0 = loc(in.p0), l1 = two ? loc(in.p1) : l0;
+        std::complex<double> M[16];
+        const int gd = two ? 4 : 2;
+        if (in.op == OP_DIAG1 || in.op == OP_DIAG2) {
+            for (int e = 0; e < 16; e++)
+                M[e] = 0.0;
+            for (int x = 0; x < gd; x++) {  // D[x] = G a0^{x0} a1^{x1} c^{x0 x1}
+                const int x0 = x & 1, x1 = (x >> 1) & 1;
+                std::complex<double> v = cx(0);
+                if (x0) v *= cx(1);
+                if (two && x1) v *= cx(2);
+                if (two && x0 && x1) v *= cx(3);
+                M[x * gd + x] = v;
+            }
+        } else {
+            for (int e = 0; e < gd * gd; e++)
+                M[e] = cx(e);
+        }
+        const uint32_t gmask = two ? ((1u << l0) | (1u << l1)) : (1u << l0);
+        for (uint32_t r = 0; r < d; r++)
+            for (uint32_t c = 0; c < d; c++) {
+                std::complex<double> acc = 0.0;
+                const int kr = (int)(((r >> l0) & 1u) | (two ? (((r >> l1) & 1u) << 1) : 0u));
+                for (uint32_t x = 0; x < d; x++) {
+                    if ((x & ~gmask) != (r & ~gmask))
+                        continue;
+                    const int kx = (int)(((x >> l0) & 1u) | (two ? (((x >> l1) & 1u) << 1) : 0u));
+                    acc += M[kr * gd + kx] * U[x * d + c];
+                }
+                T[r * d + c] = acc;
+            }
+        U.swap(T);
+    }
+    return U;
+}
+
+// Tensor-core operand of a fused gate: the real 2^(k+1)-square matrix
+// [[Re U, -Im U], [Im U, Re U]] as TF32 hi and lo parts, each in the K-major
+// core-matrix layout (8 rows x 16 bytes per core matrix; core matrices adjacent
+// in K are 128 bytes apart, 8-row groups K/4 * 128 bytes apart).
+static void append_fused_operand(std::vector<float> &out, const std::vector<std::complex<double>> &U, uint32_t k)
+{
+    const uint32_t d = 1u << k, K = 2 * d;
+    const size_t base = out.size();
+    out.resize(base + 2 * (size_t)K * K, 0.f);
+    for (uint32_t o = 0; o < K; o++)
+        for (uint32_t kk = 0; kk < K; kk++) {
+            const std::complex<double> u = U[(o % d) * d + (kk % d)];
+            double val;
+            if (o < d)
+                val = kk < d ? u.real() : -u.imag();
+            else
+                val = kk < d ? u.imag() : u.real();
+            const float f = (float)val, hi = tf32_round(f), lo = tf32_round(f - hi);
+            const size_t off = (size_t)(o / 8) * (K / 4) * 32 + (size_t)(kk / 4) * 32 + (o % 8) * 4 + (kk % 4);
+            out[base + off] = hi;
+            out[base + (size_t)K * K + off] = lo;
+        }
+}
+
 // Lower every pass into the record program the kernels walk (see RecHdr):
 // dense gates with their matrix inline, and each run of consecutive diagonal
 // gates (lazy SWAPs included) merged into one record of per-qubit and
 // per-pair factors classified by the tile position of their bits.
+#ifndef TQS_FUSE_MIN_DENSE
+#define TQS_FUSE_MIN_DENSE 2  // dense gates a block needs before it is fused onto the tensor cores
+#endif
 static void compile_programs(PlanHost &P)
 {
     const bool f64 = P.prec == TQS_FP64;
@@ -315,6 +412,8 @@ static void compile_programs(PlanHost &P)
     std::vector<uint8_t> &out = P.prog;
     out.clear();
     P.chunk_off.clear();
+    P.fused.clear();
+    P.fused_k = 0;
     auto put = [&](const void *p, size_t n) {
         const uint8_t *b = (const uint8_t *)p;
         out.insert(out.end(), b, b + n);
@@ -349,13 +448,71 @@ static void compile_programs(PlanHost &P)
             pos[ps.tbits[j]] = (uint8_t)j;
         auto is_slot = [&](uint8_t p) { return pos[p] != 0xff && pos[p] >= 8; };
         ps.chunk_begin = (uint32_t)P.chunk_off.size();
+        ps.fused_blocks = 0;
         if (ps.ibeg < ps.iend) {
             P.chunk_off.push_back((uint32_t)out.size());
             chunk_start = out.size();
         }
+        // tensor-core fusion: FP32 states and tiles with 128 columns beside k = t - 7 fused qubits
+        const uint32_t kf = (P.fuse && !f64 && (ps.t == 11 || ps.t == 12)) ? ps.t - 7 : 0;
         uint32_t k = ps.ibeg;
         while (k < ps.iend) {
             const Instr &in = P.instrs[k];
+            if (kf && (in.op == OP_DENSE1 || in.op == OP_DENSE2)) {
+                uint32_t qmask = 0, dense_cnt = 0, kk = k;
+                for (; kk < ps.iend; kk++) {
+                    const Instr &g = P.instrs[kk];
+                    if (g.op == OP_NOP)
+                        continue;
+                    const bool two = g.op == OP_DENSE2 || g.op == OP_DIAG2;
+                    const uint32_t gm = (1u << g.p0) | (two ? (1u << g.p1) : 0u);
+                    if (pos[g.p0] == 0xff || (two && pos[g.p1] == 0xff))
+                        break;
+                    if ((uint32_t)__builtin_popcount(qmask | gm) > kf)
+                        break;
+                    qmask |= gm;
+                    dense_cnt += (g.op == OP_DENSE1 || g.op == OP_DENSE2) ? 1 : 0;
+                }
+                if (dense_cnt >= (uint32_t)TQS_FUSE_MIN_DENSE) {
+                    // pad the fused set to exactly kf tile qubits (identity on the extra ones)
+                    for (uint32_t j = 0; j < ps.t && (uint32_t)__builtin_popcount(qmask) < kf; j++)
+                        qmask |= 1u << ps.tbits[j];
+                    uint8_t q[8] = {0}, jp[8] = {0};
+                    uint32_t nq = 0;
+                    for (uint32_t b = 0; b < 32; b++)
+                        if (qmask & (1u << b)) {
+                            q[nq] = (uint8_t)b;
+                            jp[nq] = pos[b];
+                            nq++;
+                        }
+                    std::vector<uint32_t> ids;
+                    for (uint32_t x = k; x < kk; x++)
+                        ids.push_back(x);
+                    const uint32_t off = (uint32_t)P.fused.size();
+                    append_fused_operand(P.fused, fused_unitary(P, ids, q, kf), kf);
+                    P.fused_k = kf;
+                    ps.fused_blocks++;
+                    reserve(48);
+                    RecHdr h;
+                    std::memset(&h, 0, sizeof(h));
+                    h.type = REC_FUSED;
+                    h.a = (uint8_t)kf;
+                    h.site = in.site;
+                    h.ibeg = k;
+                    h.iend = kk;
+                    put(&h, 16);
+                    uint8_t pj[16] = {0};
+                    for (uint32_t i = 0; i < 8; i++) {
+                        pj[i] = jp[i];
+                        pj[8 + i] = q[i];
+                    }
+                    put(pj, 16);
+                    uint32_t w4[4] = {off, 0, 0, 0};
+                    put(w4, 16);
+                    k = kk;
+                    continue;
+                }
+            }
             if (in.op == OP_DENSE1 || in.op == OP_DENSE2) {
                 const bool two = in.op == OP_DENSE2;
                 reserve(16 + (two ? 16 : 4) * csz);
@@ -706,6 +863,7 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
     for (uint32_t r = 0; r < S.gamma; r++)
         if (S.rank_q[r] != r)
             return "internal: sampler layout invariant broken";
+    P.fuse = (o.flags & TQS_FLAG_FUSE) != 0;
     compile_programs(P);
     return "";
 }

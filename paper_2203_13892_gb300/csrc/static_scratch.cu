@@ -144,6 +144,10 @@ extern "C" tqs_status tqs_simulate_static(const tqs_circuit *c, const tqs_noise 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dp.d_chunk_off, H.chunk_off.data(), 4 * H.chunk_off.size(), cudaMemcpyHostToDevice,
                             dp.stream);
+    if (e == cudaSuccess && !H.fused.empty())
+        e = cudaMemcpyAsync(dp.d_fused, H.fused.data(), 4 * H.fused.size(), cudaMemcpyHostToDevice, dp.stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(dp.d_err, 0, 4 * sizeof(unsigned int), dp.stream);
     uint8_t perm[32] = {0};
     for (uint32_t q = 0; q < H.n; q++)
         perm[q] = H.levels.back().perm[q];
@@ -159,5 +163,6 @@ extern "C" tqs_status tqs_simulate_static(const tqs_circuit *c, const tqs_noise 
     e = cudaStreamSynchronize(dp.stream);
     if (e != cudaSuccess)
         return tqs::set_error(TQS_ECUDA, tqs::cuda_msg("tqs_simulate_static", (int)e));
-    return TQS_OK;
+    st = dp.check_device_error(err);
+    return st == TQS_OK ? TQS_OK : tqs::set_error(st, err);
 }

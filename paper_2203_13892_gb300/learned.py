@@ -35,20 +35,37 @@ def training_circuit(i: int, base: int = 100000, n_range=(12, 22), layers=(20, 6
     return random_layers(n, L, base + i)
 
 
-def time_tree(c, nz, shots, arity, split, prec="fp32", trial_leaves=4096, reps=1):
-    """ms per leaf of `arity`/`split` measured on whole level-0 subtrees."""
+_WS = {}
+
+
+def _workspace(nbytes=4 << 30):
+    """One device workspace (and histogram) reused by every trial run."""
     import torch
 
+    if "ws" not in _WS:
+        _WS["ws"] = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        _WS["counts"] = torch.zeros(1 << 24, dtype=torch.int64, device="cuda")
+    return _WS["ws"], _WS["counts"]
+
+
+def trial_leaves_for(n: int) -> int:
+    """Leaves timed per candidate: about 2^26 amplitude-leaves of work at any n."""
+    return int(min(4096, max(64, 1 << max(0, 26 - n))))
+
+
+def time_tree(c, nz, shots, arity, split, prec="fp32", trial_leaves=4096, reps=1, warmup=0):
+    """ms per leaf of `arity`/`split` measured on whole level-0 subtrees."""
     below = int(np.prod(arity[1:])) if len(arity) > 1 else 1
     roots = max(1, min(-(-shots // below), max(1, trial_leaves // below)))
     leaves = min(shots, roots * below)
-    o = capi.options(arity=arity, split=split, prec=prec, flags=capi.TQS_FLAG_NO_FIDELITY)
+    ws, d = _workspace()
+    o = capi.options(arity=arity, split=split, prec=prec, flags=capi.TQS_FLAG_NO_FIDELITY,
+                     workspace=ws.data_ptr(), workspace_bytes=ws.numel())
     plan = capi.tqs_plan_create(c, nz, leaves, o)
-    d = torch.zeros(1 << 24, dtype=torch.int64, device="cuda")
     best = float("inf")
-    for r in range(reps + 1):
+    for r in range(warmup + reps):
         rep = capi.tqs_plan_execute(plan, r, d.data_ptr(), report=True)
-        if r:
+        if r >= warmup:
             best = min(best, rep["kernel_ms"] / leaves)
     plan.close()
     return best
@@ -62,7 +79,7 @@ def label_circuit(circ, shots, prec="fp32"):
     times = np.full(capi.TQS_LEARNED_CLASSES, np.inf)
     for cls in np.nonzero(allowed)[0]:
         arity, split = capi.tqs_learned_candidate(c, nz, shots, o, int(cls))
-        times[cls] = time_tree(c, nz, shots, arity, split, prec)
+        times[cls] = time_tree(c, nz, shots, arity, split, prec, trial_leaves_for(circ.n))
     return feat, allowed, times
 
 
@@ -113,8 +130,8 @@ def evaluate(w, count=200, shots=8192, base=200000, n_range=(20, 24), layers=(20
                 counts, F, rep = capi.tqs_simulate(c, nz, shots, 11, o, n=circ.n)
                 res[part] = {"tree": arity, "split": split, "shots_per_s": rep["shots_per_s"], "F": F}
             else:
-                res[part] = {"tree": arity, "split": split,
-                             "shots_per_s": 1.0 / time_tree(c, nz, shots, arity, split, prec) * 1e3}
+                ms = time_tree(c, nz, shots, arity, split, prec, trial_leaves_for(circ.n), reps=2, warmup=1)
+                res[part] = {"tree": arity, "split": split, "shots_per_s": 1e3 / ms}
         rows.append({"n": circ.n, "gates": len(circ.gates), **res})
     capi.tqs_learned_set_model(None)
     return rows
