@@ -39,10 +39,10 @@ P1, P2, PM = 1e-3, 1e-2, 2e-2
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
-def workload_config(tree=None, split=None, extra=None):
+def workload_config(tree=None, split=None, extra=None, shots=SHOTS):
     cfg = {
-        "workload": "qft20_noisy_tree_fp32_dcp_32000shots",
-        "n_qubits": N_QUBITS, "gates": 220, "shots_per_step": SHOTS,
+        "workload": f"qft20_noisy_tree_fp32_dcp_{shots}shots",
+        "n_qubits": N_QUBITS, "gates": 220, "shots_per_step": shots,
         "noise": {"p1": P1, "p2": P2, "pm": PM, "channel": "depolarizing+readout"},
         "mode": "tree", "precision": "fp32", "partitioner": "dcp",
         "input": "|0...0>", "l2": "512 MiB buffer written between timed steps",
@@ -71,9 +71,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kind):
-    """Per-launch DRAM bytes of kernel class `kind` from the committed ncu summary,
-    or None when the kernels changed since it was captured."""
+def recorded_traffic(kind, alg_bytes_per_launch):
+    """DRAM bytes per launch of kernel class `kind`, from the committed ncu
+    capture of a small case of the same kernel: its DRAM bytes per CTA (one
+    tile of one node) times the CTAs of a full launch, or None when the kernels
+    changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic_qft20_tree_fp32.json")
     if not os.path.exists(p):
         return None
@@ -81,7 +83,10 @@ def recorded_traffic(kind):
     if d.get("source_hash") != kernel_source_hash():
         return None
     ent = d.get("kernels", {}).get(kind)
-    return None if ent is None else ent.get("dram_bytes_per_launch")
+    if not ent:
+        return None
+    ctas = alg_bytes_per_launch / ent["alg_bytes_per_cta"]
+    return ent["dram_bytes_per_cta"] * ctas
 
 
 class ClockSampler:
@@ -182,21 +187,21 @@ def oracle_sample(arity, split, subtrees, threads, seed=0):
     return leaves, dt
 
 
-def dcp_tree():
+def dcp_tree(shots=SHOTS):
     """DCP tree of the workload (host-only call into the library)."""
     import paper_2203_13892_gb300 as tqs
     from tqs_inputs import qft
 
     c = tqs.circuit(qft(N_QUBITS))
     nz = tqs.tqs_noise_model(P1, P2, PM)
-    return tqs.tqs_partition(c, nz, SHOTS, tqs.options())
+    return tqs.tqs_partition(c, nz, shots, tqs.options())
 
 
 def run_reference(args, dist, world, rank):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
-    arity, split = dcp_tree()
+    arity, split = dcp_tree(args.shots)
     subtrees = max(1, cores)
     steps = []
     for i in range(args.warmup + args.steps):
@@ -212,7 +217,7 @@ def run_reference(args, dist, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(arity, split, {"l2": "host run"}),
+        "data": "synthetic", "config": workload_config(arity, split, {"l2": "host run"}, args.shots),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -229,6 +234,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--baseline-shots", type=int, default=2000,
                     help="shots of the FP64 baseline-mode comparison run")
+    ap.add_argument("--shots", type=int, default=SHOTS,
+                    help="shots per step (smaller values make the small case of a profiler capture)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="tree nodes per launch (0: the library's choice)")
     args = ap.parse_args()
     dist, world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -254,8 +263,10 @@ def main():
     nz = tqs.tqs_noise_model(P1, P2, PM)
     seed0 = args.seed + 1000003 * rank
 
+    SH = args.shots
+
     def make_plan(shots, **kw):
-        o = tqs.options(stream=stream.cuda_stream, **kw)
+        o = tqs.options(stream=stream.cuda_stream, batch=args.batch, **kw)
         probe = tqs.tqs_plan_create(c, nz, shots, o)
         nbytes = tqs.tqs_plan_workspace_bytes(probe)
         probe.close()
@@ -264,7 +275,7 @@ def main():
         o.workspace_bytes = nbytes
         return tqs.tqs_plan_create(c, nz, shots, o), ws
 
-    plan, ws = make_plan(SHOTS, flags=capi.TQS_FLAG_PROFILE)
+    plan, ws = make_plan(SH, flags=capi.TQS_FLAG_PROFILE)
     d_counts = torch.zeros(1 << N_QUBITS, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -295,9 +306,9 @@ def main():
         dist.barrier()
     for a, b in ev:
         step_ms.append(a.elapsed_time(b))
-    assert int(d_counts.sum().item()) == SHOTS
+    assert int(d_counts.sum().item()) == SH
     total_ms = max_over_ranks(dist, sum(step_ms))
-    total_shots = sum_over_ranks(dist, SHOTS * args.steps)
+    total_shots = sum_over_ranks(dist, SH * args.steps)
     value = total_shots / (total_ms * 1e-3)
 
     # ---- dominant kernel and roofline --------------------------------
@@ -334,18 +345,18 @@ def main():
     del bplan, bws, bcounts
 
     # ---- end to end through the public call with host buffers --------
-    o = tqs.options(stream=stream.cuda_stream)
+    o = tqs.options(stream=stream.cuda_stream, batch=args.batch)
     o.workspace = ws.data_ptr()
     o.workspace_bytes = ws.numel()
     del plan
-    tqs.tqs_simulate(c, nz, SHOTS, 99, o, n=N_QUBITS)  # warm
+    tqs.tqs_simulate(c, nz, SH, 99, o, n=N_QUBITS)  # warm
     torch.cuda.synchronize()
     e2e_s = []
     for k in range(args.steps):
         t0 = time.perf_counter()
-        counts, fid, _ = tqs.tqs_simulate(c, nz, SHOTS, 100 + k, o, n=N_QUBITS)
+        counts, fid, _ = tqs.tqs_simulate(c, nz, SH, 100 + k, o, n=N_QUBITS)
         e2e_s.append(time.perf_counter() - t0)
-        assert int(counts.sum()) == SHOTS
+        assert int(counts.sum()) == SH
     e2e_time = max_over_ranks(dist, sum(e2e_s))
     e2e_value = total_shots / e2e_time
     G = len(circ.gates)
@@ -370,10 +381,10 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(rep0["arity"], rep0["split"],
                                   {"parallelism": f"independent problem per GPU x{world}",
-                                   "passes_per_level": rep0["passes"]}),
+                                   "passes_per_level": rep0["passes"]}, SH),
         "roofline": {"bound": "hbm", "kernel": f"pass_kernel[{dom}]", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic(dom), "alg_bytes_per_launch": per_launch_bytes,
+                     "traffic": recorded_traffic(dom, per_launch_bytes), "alg_bytes_per_launch": per_launch_bytes,
                      "avg_launch_ms": avg_s * 1e3, "launches": D["launches"]},
         "kernel_classes": {n: {"launches": d["launches"], "ms_per_step": d["ms"] / args.steps,
                                "GBps": (d["bytes"] / (d["ms"] * 1e-3) / 1e9) if d["ms"] > 0 else None}
