@@ -610,7 +610,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     }
 
     const SamplerLayout &SL = a.samp;
-    if (MODE != MODE_STORE) {
+    if (MODE == MODE_SUMS) {
+        // rank (position in ascending logical order) of each tile position
+        if (tid < a.t)
+            lut[SL.rank_pos[tid]] = (uint16_t)tid;
+    }
+    if (MODE == MODE_SAMPLE) {
         // unkey tables: rank bits 0..6 -> tile positions (lut[0..127]), 7..13 -> lut[128..255]
         for (uint32_t i = tid; i < 256; i += kThreads) {
             const uint32_t rb = i < 128 ? 0 : 7, vv = i & 127;
@@ -711,6 +716,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
         for (uint32_t x = tid; x < a.sites; x += kThreads)
             nzs[x] = nzg[x];
     auto noise_at = [&](uint32_t site) -> uint32_t { return nz_staged ? nzs[site] : nzg[site]; };
+    // does any of the `ns` sites from `s0` hold a Pauli?  (the lanes split the sites)
+    auto sites_noisy = [&](uint32_t s0, uint32_t ns) -> bool {
+        uint32_t any = 0;
+        for (uint32_t x = tid & 31u; x < ns; x += 32u)
+            any |= noise_at(s0 + x);
+        return __any_sync(0xffffffffu, any != 0u);
+    };
     DiagAcc<C, LOGR> acc;
     acc.reset();
     bool pending = false;
@@ -1025,10 +1037,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                     if (tid == 0 && a.err)
                         atomicOr(a.err, 2u);
                   } else {
-                    const uint32_t nsites = hiend - hibeg;
-                    uint32_t any = 0;
-                    for (uint32_t x = 0; x < nsites; x++)
-                        any |= noise_at(hsite + x);
+                    const bool any = sites_noisy(hsite, hiend - hibeg);
                     bool done = false;
                     if constexpr (sizeof(R) == 4) {
                         if (!any && a.fused_k == ha) {
@@ -1057,11 +1066,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                     p += 48u;
                 } else {
                     const uint32_t nfac = ha + hb + hc + hd + he;
-                    const uint32_t nsites = hiend - hibeg;
-                    uint32_t any = 0;
-                    for (uint32_t x = 0; x < nsites; x++)
-                        any |= noise_at(hsite + x);
-                    if (!any) {
+                    if (!sites_noisy(hsite, hiend - hibeg)) {
                         acc.base = cmul(acc.base, pc(0));
                         const unsigned char *fp = pay + 16;
                         constexpr uint32_t FS = CS == 8 ? 16u : 32u;
@@ -1151,63 +1156,92 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     };
 
     if (MODE == MODE_SUMS) {
-        // Block sums of |a|^2 over the 2^gamma amplitudes that differ only in the
-        // tile positions holding the lowest gamma logical bits (mask wpos):
-        // butterfly additions over register slots, then lanes (shuffles), then
-        // warp bits (shared memory), in the state's precision (a pairwise order);
-        // each block sum leaves as one FP64 value.
-        uint32_t wpos = 0;
-        for (uint32_t r = 0; r < SL.gamma; r++)
-            wpos |= 1u << SL.rank_pos[r];
-        R pr[NR];
-#pragma unroll
-        for (int k = 0; k < NR; k++)
-            pr[k] = norm2<R>(v[k]);
+        // Block sums of |a|^2 over the 2^gamma outcomes that share every logical
+        // bit above gamma.  Each |a|^2 is staged in shared memory at its logical
+        // tile index (tile element ^ frame, bits in rank = ascending logical
+        // order), so block b of this tile is the run [b 2^gamma, (b+1) 2^gamma).
+        // Each thread adds its run of consecutive values, the threads of one
+        // block combine with shuffles, and one thread per block writes the sum
+        // as FP64.  The index map is linear over XOR: thread part ^ slot part.
+        uint32_t Lt = 0;
+        {
+            const uint32_t et = tid ^ (mT & 0xffu), tb = a.t < 8u ? a.t : 8u;
+            for (uint32_t j = 0; j < tb; j++)
+                Lt |= ((et >> j) & 1u) << lut[j];
+        }
+        uint32_t img[LOGR > 0 ? LOGR : 1];
 #pragma unroll
         for (int sb = 0; sb < LOGR; sb++) {
-            if ((wpos >> (8 + sb)) & 1u) {
+            img[sb] = 1u << lut[8 + sb];
+            if ((mT >> (8 + sb)) & 1u)
+                Lt ^= img[sb];
+        }
+        R *P = reinterpret_cast<R *>(s);
+        // bank swizzle: folds the index bits above the 32 banks into the bank
+        // bits, so the scattered writes (a permutation of the tile bits) and the
+        // runs read per thread both spread over the banks
+        auto sw = [](uint32_t L) { return L ^ (((L >> 5) ^ (L >> 10)) & 31u); };
+        __syncthreads();
+        if (active) {
 #pragma unroll
-                for (int k = 0; k < NR; k++)
-                    if (!((k >> sb) & 1))
-                        pr[k] += pr[k | (1 << sb)];
+            for (int k = 0; k < NR; k++) {
+                uint32_t L = Lt;
+#pragma unroll
+                for (int sb = 0; sb < LOGR; sb++)
+                    if ((k >> sb) & 1)
+                        L ^= img[sb];
+                P[sw(L)] = norm2<R>(v[k]);
             }
         }
-        for (uint32_t j = 0; j < 5; j++) {
-            if ((wpos >> j) & 1u) {
-#pragma unroll
-                for (int k = 0; k < NR; k++)
-                    pr[k] += __shfl_xor_sync(0xffffffffu, pr[k], 1 << j);
-            }
-        }
-        R *sr = reinterpret_cast<R *>(s);
-        for (uint32_t j = 5; j < 8; j++) {
-            if ((wpos >> j) & 1u) {
-                __syncthreads();
-#pragma unroll
-                for (int k = 0; k < NR; k++)
-                    sr[tid + k * kThreads] = pr[k];
-                __syncthreads();
-#pragma unroll
-                for (int k = 0; k < NR; k++)
-                    pr[k] += sr[(tid ^ (1u << j)) + k * kThreads];
-            }
-        }
-        // the representative of each block (all gamma low logical bits physically 0
-        // in tile coordinates) writes it; its block index is its higher logical bits
         uint64_t hpart = 0;
         for (uint32_t b = 0; b < a.n - a.t; b++) {
             const uint32_t pb = a.hbits[b];
             hpart |= (uint64_t)(((base ^ mask) >> pb) & 1u) << (SL.logical_of_hbit[b] - SL.gamma);
         }
-        if (active && (tid & wpos) == 0) {
+        const uint32_t gam = SL.gamma, B = 1u << gam;
+        // block index of this tile's block bl: its bits deposited at the logical bits above gamma
+        auto block_index = [&](uint32_t bl) -> uint64_t {
+            uint64_t g = hpart;
+            for (uint32_t i = 0; bl; i++, bl >>= 1)
+                if (bl & 1u)
+                    g |= (uint64_t)1 << (SL.rank_q[gam + i] - gam);
+            return g;
+        };
+        double *Srow = a.S + (uint64_t)slot * SL.groups;
+        const uint32_t nper = TE < (uint32_t)kThreads ? 1u : (uint32_t)NR;  // values per thread
+        const uint32_t e0 = tid * nper;
+        __syncthreads();
+        if (B <= nper) {  // whole blocks inside each thread's run
+            if (e0 < TE)
+                for (uint32_t b0 = 0; b0 < nper; b0 += B) {
+                    R acc = (R)0;
+                    for (uint32_t i = 0; i < B; i++)
+                        acc += P[sw(e0 + b0 + i)];
+                    Srow[block_index((e0 + b0) >> gam)] = (double)acc;
+                }
+        } else {
+            R acc = (R)0;
+            if (e0 < TE) {
 #pragma unroll
-            for (int k = 0; k < NR; k++) {
-                if ((((uint32_t)k << 8) & wpos) == 0) {
-                    const uint32_t e = (tid + (uint32_t)k * kThreads) ^ mT;  // logical tile bits
-                    uint64_t g = hpart;
-                    for (uint32_t r = SL.gamma; r < a.t; r++)
-                        g |= (uint64_t)((e >> SL.rank_pos[r]) & 1u) << (SL.rank_q[r] - SL.gamma);
-                    a.S[(uint64_t)slot * SL.groups + g] = (double)pr[k];
+                for (int i = 0; i < NR; i++)
+                    if ((uint32_t)i < nper)
+                        acc += P[sw(e0 + (uint32_t)i)];
+            }
+            const uint32_t tpb = B / nper;  // threads per block
+            if (tpb <= 32u) {
+                for (uint32_t off = 1; off < tpb; off <<= 1)
+                    acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                if (e0 < TE && (tid & (tpb - 1u)) == 0)
+                    Srow[block_index(e0 >> gam)] = (double)acc;
+            } else {
+                R *part = reinterpret_cast<R *>(red);
+                part[tid] = acc;
+                __syncthreads();
+                if (e0 < TE && (tid & (tpb - 1u)) == 0) {
+                    R t2 = (R)0;
+                    for (uint32_t i = 0; i < tpb; i++)
+                        t2 += part[tid + i];
+                    Srow[block_index(e0 >> gam)] = (double)t2;
                 }
             }
         }
