@@ -94,7 +94,7 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
         off = align256(off + bytes);
         return o;
     };
-    size_t o_instr = take(sizeof(Instr) * std::max<size_t>(H.instrs.size(), 1));
+    size_t o_instr = take(2 * sizeof(Instr) * std::max<size_t>(H.instrs.size(), 1));
     size_t o_mats = take((H.prec == TQS_FP64 ? 8 : 4) * H.mats64.size());
     size_t o_pst = take(sizeof(uint32_t) * (H.passes.size() + L) + 64);
     size_t o_prog = take(std::max<size_t>(H.prog.size(), 16));
@@ -118,6 +118,7 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
     if (assign) {
         char *b = (char *)ws;
         d_instr = (Instr *)(b + o_instr);
+        d_pinstr = d_instr + std::max<size_t>(H.instrs.size(), 1);
         d_mats = b + o_mats;
         d_pass_start = (uint32_t *)(b + o_pst);
         d_prog = (uint8_t *)(b + o_prog);
@@ -187,6 +188,8 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
     layout(B, true);
     // uploads
     CK(cudaMemcpyAsync(d_instr, H.instrs.data(), sizeof(Instr) * H.instrs.size(), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_pinstr, H.prog_instrs.data(), sizeof(Instr) * H.prog_instrs.size(), cudaMemcpyHostToDevice,
+                       stream));
     if (H.prec == TQS_FP64)
         CK(cudaMemcpyAsync(d_mats, H.mats64.data(), 8 * H.mats64.size(), cudaMemcpyHostToDevice, stream));
     else
@@ -261,7 +264,7 @@ tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vect
         a.parent_lo = i ? plo[i - 1] : 0;
         a.arity = lv.arity;
         a.nnodes = (uint32_t)nn;
-        a.instr = d_instr;
+        a.instr = d_pinstr;
         a.ibeg = ps.ibeg;
         a.iend = ps.iend;
         a.prog = d_prog;
@@ -391,7 +394,7 @@ tqs_status DevicePlan::run_chain(uint32_t level, uint64_t node, uint64_t seed, s
             a.parent_lo = i ? plo[i - 1] : 0;
             a.arity = lv.arity;
             a.nnodes = 1;
-            a.instr = d_instr;
+            a.instr = d_pinstr;
             a.ibeg = ps.ibeg;
             a.iend = ps.iend;
             a.prog = d_prog;

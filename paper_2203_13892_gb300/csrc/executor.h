@@ -22,7 +22,8 @@ struct DevicePlan {
     void *ws = nullptr;
     size_t ws_bytes = 0;
     bool own_ws = false;
-    Instr *d_instr = nullptr;
+    Instr *d_instr = nullptr;   // site order (noise kernel)
+    Instr *d_pinstr = nullptr;  // program order (pass kernels)
     void *d_mats = nullptr;
     uint32_t *d_pass_start = nullptr;
     uint8_t *d_prog = nullptr;

@@ -68,7 +68,8 @@ struct Noise {
 //   REC_DENSE2  a=j0 b=j1 c=p0 d=p1     payload U[4x4]             noise site `site`
 //   REC_RUN     a..e = factor counts    payload G, then factors    sites [ibeg, iend) of the
 //               of kinds A_FIXED, A_SLOT, C_FIXED, C_MIXED, C_SLOTS (in that order) for the
-//               run of consecutive diagonal gates (and lazy SWAPs) it aggregates
+//               run of consecutive diagonal gates (and lazy SWAPs) it aggregates, then one
+//               GateEnt (+ 4 factors) per gate of the run
 // DENSE1 sets c = 1 when the matrix is real.  A factor record is an 8-byte FacHdr
 // followed by its complex value at the next multiple of sizeof(C) (16 or 32 bytes).
 // A run's factors: the product over its gates of D = G * prod a_q^{x_q} *
@@ -95,6 +96,16 @@ struct RecHdr {
     uint32_t ibeg, iend;  // instruction range (the run's gates, for the per-gate fallback)
 };
 static_assert(sizeof(RecHdr) == 16, "RecHdr layout");
+// A REC_RUN record ends with one GateEnt per gate of the run, each followed by
+// the gate's four diagonal factors (G, a0, a1, c) in the state's precision: the
+// path for nodes that hold a Pauli inside the run (the frame may change mid-run).
+struct GateEnt {
+    uint8_t op, fl, j0, p0;   // fl: bit k set iff factor k != 1 (as Instr::pad)
+    uint8_t j1, p1, np0, np1;
+    uint8_t npaulis, pad0, pad1, pad2;
+    uint32_t site;
+};
+static_assert(sizeof(GateEnt) == 16, "GateEnt layout");
 struct FacHdr {
     uint8_t kind, j0, p0, j1, p1, pad0, pad1, pad2;
 };
@@ -139,7 +150,8 @@ struct PlanHost {
     uint64_t shots;
     std::vector<Level> levels;
     std::vector<Pass> passes;
-    std::vector<Instr> instrs;
+    std::vector<Instr> instrs;       // per pass in site order (the noise kernel's table)
+    std::vector<Instr> prog_instrs;  // per pass in program order (diagonal gates sunk)
     std::vector<double> mats64;    // 32 doubles per gate
     std::vector<float> mats32;     // 32 floats per gate
     std::vector<uint8_t> prog;     // compiled pass programs (state precision), all passes

@@ -380,7 +380,9 @@ template <typename C, int NS> struct DiagAcc {
     C E[NS > 0 ? NS : 1];
     C Gs[NS > 1 ? NS * (NS - 1) / 2 : 1];
     bool has_gs;
-    uint32_t e_used;  // slot factors that some gate touched (uniform)
+    bool base_used;    // some factor went to `base` (uniform, whatever its condition gave)
+    uint32_t e_used;   // slot factors that some gate touched (uniform)
+    uint32_t gs_used;  // slot pairs that some gate touched (uniform)
     __device__ __forceinline__ void reset()
     {
         base = mk((decltype(base.x))1, (decltype(base.x))0);
@@ -391,7 +393,9 @@ template <typename C, int NS> struct DiagAcc {
         for (int i = 0; i < (NS > 1 ? NS * (NS - 1) / 2 : 1); i++)
             Gs[i] = base;
         has_gs = false;
+        base_used = false;
         e_used = 0;
+        gs_used = 0;
     }
     __device__ __forceinline__ void mul_E(int s, C f)
     {
@@ -414,6 +418,7 @@ template <typename C, int NS> struct DiagAcc {
             if (k == idx)
                 Gs[k] = cmul(Gs[k], f);
         has_gs = true;
+        gs_used |= 1u << idx;
         e_used |= (1u << s0) | (1u << s1);
     }
 };
@@ -425,6 +430,7 @@ template <typename C, int NS>
 __device__ __forceinline__ void acc_alpha(DiagAcc<C, NS> &A, uint32_t j, uint32_t p, uint32_t xt, C f)
 {
     if (thread_or_outside(j)) {
+        A.base_used = true;
         if ((xt >> p) & 1u)
             A.base = cmul(A.base, f);
     } else {
@@ -438,6 +444,7 @@ __device__ __forceinline__ void acc_gamma(DiagAcc<C, NS> &A, uint32_t j0, uint32
 {
     const bool a = thread_or_outside(j0), b = thread_or_outside(j1);
     if (a && b) {
+        A.base_used = true;
         if ((xt >> p0) & (xt >> p1) & 1u)
             A.base = cmul(A.base, f);
     } else if (a) {
@@ -471,6 +478,7 @@ __device__ __forceinline__ void acc_flush(DiagAcc<C, LOGR> &A, C (&v)[1 << LOGR]
             Eb[s] = A.E[s];
         }
     }
+    bool bmul = A.base_used || (msig & A.e_used) != 0u;  // uniform: does base differ from 1?
     C Gb[LOGR > 1 ? LOGR * (LOGR - 1) / 2 : 1];
     if (A.has_gs) {
 #pragma unroll
@@ -478,6 +486,10 @@ __device__ __forceinline__ void acc_flush(DiagAcc<C, LOGR> &A, C (&v)[1 << LOGR]
 #pragma unroll
             for (int lo = 0; lo < hi; lo++) {
                 const int idx = hi * (hi - 1) / 2 + lo;
+                if (!((A.gs_used >> idx) & 1u)) {
+                    Gb[idx] = A.Gs[idx];
+                    continue;
+                }
                 const C g = A.Gs[idx];
                 const uint32_t mh = (msig >> hi) & 1u, ml = (msig >> lo) & 1u;
                 if (!mh && !ml) {
@@ -490,6 +502,7 @@ __device__ __forceinline__ void acc_flush(DiagAcc<C, LOGR> &A, C (&v)[1 << LOGR]
                     Gb[idx] = cconj(g);
                 } else {
                     base = cmul(base, g);
+                    bmul = true;
                     Eb[lo] = cmul(Eb[lo], cconj(g));
                     Eb[hi] = cmul(Eb[hi], cconj(g));
                     Gb[idx] = g;
@@ -497,9 +510,11 @@ __device__ __forceinline__ void acc_flush(DiagAcc<C, LOGR> &A, C (&v)[1 << LOGR]
             }
     }
     // v[k] *= base * prod_{s in k} Eb[s] * prod_{s<s' in k} Gb: one pass per factor
+    if (bmul) {
 #pragma unroll
-    for (int k = 0; k < NR; k++)
-        v[k] = cmul(v[k], base);
+        for (int k = 0; k < NR; k++)
+            v[k] = cmul(v[k], base);
+    }
 #pragma unroll
     for (int sb = 0; sb < LOGR; sb++) {
         if (!((A.e_used >> sb) & 1u) && !((msig >> sb) & 1u))
@@ -513,11 +528,14 @@ __device__ __forceinline__ void acc_flush(DiagAcc<C, LOGR> &A, C (&v)[1 << LOGR]
 #pragma unroll
         for (int hi = 1; hi < LOGR; hi++)
 #pragma unroll
-            for (int lo = 0; lo < hi; lo++)
+            for (int lo = 0; lo < hi; lo++) {
+                if (!((A.gs_used >> (hi * (hi - 1) / 2 + lo)) & 1u))
+                    continue;
 #pragma unroll
                 for (int k = 0; k < NR; k++)
                     if (((k >> hi) & 1) && ((k >> lo) & 1))
                         v[k] = cmul(v[k], Gb[hi * (hi - 1) / 2 + lo]);
+            }
     }
     A.reset();
 }
@@ -716,13 +734,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
         for (uint32_t x = tid; x < a.sites; x += kThreads)
             nzs[x] = nzg[x];
     auto noise_at = [&](uint32_t site) -> uint32_t { return nz_staged ? nzs[site] : nzg[site]; };
-    // does any of the `ns` sites from `s0` hold a Pauli?  (the lanes split the sites)
-    auto sites_noisy = [&](uint32_t s0, uint32_t ns) -> bool {
-        uint32_t any = 0;
-        for (uint32_t x = tid & 31u; x < ns; x += 32u)
-            any |= noise_at(s0 + x);
-        return __any_sync(0xffffffffu, any != 0u);
-    };
+
     DiagAcc<C, LOGR> acc;
     acc.reset();
     bool pending = false;
@@ -869,8 +881,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     auto diag_gate = [&](const Instr &I) {
         const R *M = mats + (size_t)I.gate * 32;
         const uint32_t fl = I.pad;
-        if (fl & 1u)
+        if (fl & 1u) {
             acc.base = cmul(acc.base, mk(M[0], M[1]));
+            acc.base_used = true;
+        }
         if (fl & 2u)
             acc_alpha(acc, I.j0, I.p0, xt, mk(M[2], M[3]));
         if (I.op == OP_DIAG2) {
@@ -1037,7 +1051,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                     if (tid == 0 && a.err)
                         atomicOr(a.err, 2u);
                   } else {
-                    const bool any = sites_noisy(hsite, hiend - hibeg);
+                    uint32_t anyf = 0;  // the block's gates need not have consecutive sites
+                    for (uint32_t x = hibeg + (tid & 31u); x < hiend; x += 32u)
+                        anyf |= noise_at(a.instr[x].site);
+                    const bool any = __any_sync(0xffffffffu, anyf != 0u);
                     bool done = false;
                     if constexpr (sizeof(R) == 4) {
                         if (!any && a.fused_k == ha) {
@@ -1066,8 +1083,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                     p += 48u;
                 } else {
                     const uint32_t nfac = ha + hb + hc + hd + he;
-                    if (!sites_noisy(hsite, hiend - hibeg)) {
-                        acc.base = cmul(acc.base, pc(0));
+                    constexpr uint32_t ES = 16u + 4u * CS;  // GateEnt + 4 factors
+                    const unsigned char *gents = pay + 16 + nfac * (CS == 8 ? 16u : 32u);
+                    const uint32_t ngates = hiend - hibeg;
+                    uint32_t anyn = 0;  // a Pauli at any site of the run? (the lanes split the gates)
+                    for (uint32_t x = tid & 31u; x < ngates; x += 32u)
+                        anyn |= noise_at(*reinterpret_cast<const uint32_t *>(gents + x * ES + 12));
+                    if (!__any_sync(0xffffffffu, anyn != 0u)) {
+                        const C g0 = pc(0);
+                        if (g0.x != (R)1 || g0.y != (R)0) {
+                            acc.base = cmul(acc.base, g0);
+                            acc.base_used = true;
+                        }
+                        if (ha + hc)
+                            acc.base_used = true;
                         const unsigned char *fp = pay + 16;
                         constexpr uint32_t FS = CS == 8 ? 16u : 32u;
                         auto fval = [&](const unsigned char *q) -> C {
@@ -1098,17 +1127,35 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                             acc.mul_Gs((int)((w0 >> 8) & 0xffu) - 8, (int)(w0 >> 24) - 8, fval(fp));
                         }
                         pending = true;
-                    } else {
-                        for (uint32_t ii = hibeg; ii < hiend; ii++) {
-                            const Instr I = a.instr[ii];
-                            if (I.op == OP_DIAG1 || I.op == OP_DIAG2)
-                                diag_gate(I);
-                            const uint32_t pz = noise_at(I.site);
+                    } else {  // gate by gate from the entries after the factors (in shared memory)
+                        const unsigned char *gq = gents;
+                        for (uint32_t ii = 0; ii < ngates; ii++, gq += ES) {
+                            const uint4 e = *reinterpret_cast<const uint4 *>(gq);
+                            const uint32_t op = e.x & 0xffu, fl = (e.x >> 8) & 0xffu, j0 = (e.x >> 16) & 0xffu,
+                                           p0 = e.x >> 24, j1 = e.y & 0xffu, p1 = (e.y >> 8) & 0xffu,
+                                           np0 = (e.y >> 16) & 0xffu, np1 = e.y >> 24, npl = e.z & 0xffu;
+                            const C *M = reinterpret_cast<const C *>(gq + 16);
+                            if (op == OP_DIAG1 || op == OP_DIAG2) {
+                                if (fl & 1u) {
+                                    acc.base = cmul(acc.base, M[0]);
+                                    acc.base_used = true;
+                                }
+                                if (fl & 2u)
+                                    acc_alpha(acc, j0, p0, xt, M[1]);
+                                if (op == OP_DIAG2) {
+                                    if (fl & 4u)
+                                        acc_alpha(acc, j1, p1, xt, M[2]);
+                                    if (fl & 8u)
+                                        acc_gamma(acc, j0, p0, j1, p1, xt, M[3]);
+                                }
+                                pending = true;
+                            }
+                            const uint32_t pz = noise_at(e.w);
                             if (pz)
-                                apply_noise(pz, I.npaulis, I.j0, I.np0, I.j1, I.np1);
+                                apply_noise(pz, npl, j0, np0, j1, np1);
                         }
                     }
-                    p += 32u + nfac * (CS == 8 ? 16u : 32u);
+                    p += 32u + nfac * (CS == 8 ? 16u : 32u) + ngates * ES;
                 }
             }
         }

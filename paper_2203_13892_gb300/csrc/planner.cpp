@@ -331,7 +331,7 @@ static std::vector<std::complex<double>> fused_unitary(const PlanHost &P, const 
         return 0u;
     };
     for (uint32_t id : ids) {
-        const Instr &in = P.instrs[id];
+        const Instr &in = P.prog_instrs[id];
         if (in.op == OP_NOP)
             continue;
         const double *m = &P.mats64[(size_t)in.gate * 32];
@@ -401,13 +401,70 @@ static void append_fused_operand(std::vector<float> &out, const std::vector<std:
 // dense gates with their matrix inline, and each run of consecutive diagonal
 // gates (lazy SWAPs included) merged into one record of per-qubit and
 // per-pair factors classified by the tile position of their bits.
+// Physical qubits an instruction and its noise site act on.
+static uint32_t instr_qubits(const Instr &in)
+{
+    uint32_t m = 1u << in.np0;
+    if (in.npaulis == 15)
+        m |= 1u << in.np1;
+    if (in.op == OP_DENSE1 || in.op == OP_DIAG1)
+        m |= 1u << in.p0;
+    else if (in.op == OP_DENSE2 || in.op == OP_DIAG2)
+        m |= (1u << in.p0) | (1u << in.p1);
+    return m;
+}
+
+// Reorders each pass so that diagonal gates (and lazy SWAP noise sites) wait
+// until the first later dense gate that shares a qubit with them, or the end of
+// the pass.  An instruction and its noise site only move past instructions on
+// disjoint qubits, and instructions sharing a qubit keep their relative order,
+// so every node's result is unchanged (up to rounding): the Pauli drawn at a
+// site still acts between the same gates on its qubits.  Effect: the diagonal
+// run flushed before a dense gate holds only the factors that touch it, and the
+// rest merge into one run at the end of the pass.
+static void sink_diagonals(PlanHost &P)
+{
+    P.prog_instrs = P.instrs;
+    for (const Pass &ps : P.passes) {
+        std::vector<Instr> out, pend;
+        out.reserve(ps.iend - ps.ibeg);
+        for (uint32_t k = ps.ibeg; k < ps.iend; k++) {
+            const Instr &in = P.instrs[k];
+            if (in.op != OP_DENSE1 && in.op != OP_DENSE2) {
+                pend.push_back(in);
+                continue;
+            }
+            const uint32_t qd = instr_qubits(in);
+            std::vector<char> go(pend.size(), 0);
+            for (size_t i = 0; i < pend.size(); i++)
+                go[i] = (instr_qubits(pend[i]) & qd) != 0;
+            // an earlier pending instruction sharing a qubit with one that goes must go too
+            for (size_t i = pend.size(); i-- > 0;) {
+                if (!go[i])
+                    continue;
+                const uint32_t qi = instr_qubits(pend[i]);
+                for (size_t j = 0; j < i; j++)
+                    if (!go[j] && (instr_qubits(pend[j]) & qi))
+                        go[j] = 1;
+            }
+            std::vector<Instr> keep;
+            for (size_t i = 0; i < pend.size(); i++)
+                (go[i] ? out : keep).push_back(pend[i]);
+            pend.swap(keep);
+            out.push_back(in);
+        }
+        out.insert(out.end(), pend.begin(), pend.end());
+        std::copy(out.begin(), out.end(), P.prog_instrs.begin() + ps.ibeg);
+    }
+}
+
 #ifndef TQS_FUSE_MIN_DENSE
 #define TQS_FUSE_MIN_DENSE 2  // dense gates a block needs before it is fused onto the tensor cores
 #endif
 static void compile_programs(PlanHost &P)
 {
     const bool f64 = P.prec == TQS_FP64;
-    const size_t csz = f64 ? 16 : 8, fsz = f64 ? 32 : 16;
+    const size_t csz = f64 ? 16 : 8, fsz = f64 ? 32 : 16, esz = 16 + 4 * csz;
     const size_t kMaxFactors = 200;
     std::vector<uint8_t> &out = P.prog;
     out.clear();
@@ -457,11 +514,11 @@ static void compile_programs(PlanHost &P)
         const uint32_t kf = (P.fuse && !f64 && (ps.t == 11 || ps.t == 12)) ? ps.t - 7 : 0;
         uint32_t k = ps.ibeg;
         while (k < ps.iend) {
-            const Instr &in = P.instrs[k];
+            const Instr &in = P.prog_instrs[k];
             if (kf && (in.op == OP_DENSE1 || in.op == OP_DENSE2)) {
                 uint32_t qmask = 0, dense_cnt = 0, kk = k;
                 for (; kk < ps.iend; kk++) {
-                    const Instr &g = P.instrs[kk];
+                    const Instr &g = P.prog_instrs[kk];
                     if (g.op == OP_NOP)
                         continue;
                     const bool two = g.op == OP_DENSE2 || g.op == OP_DIAG2;
@@ -556,9 +613,19 @@ static void compile_programs(PlanHost &P)
                 pairs.push_back({{a, b}, f});
             };
             const uint32_t r0 = k;
-            while (k < ps.iend && P.instrs[k].op != OP_DENSE1 && P.instrs[k].op != OP_DENSE2 &&
-                   pairs.size() + 32 < kMaxFactors) {
-                const Instr &d = P.instrs[k];
+            // the record (header, G, factors, one gate entry per gate) must fit one chunk
+            uint32_t touched = 0;
+            auto fits_one_more = [&]() {
+                const size_t nfac = (size_t)__builtin_popcount(touched) + pairs.size() + 3;
+                return 32 + nfac * fsz + (size_t)(k - r0 + 1) * esz + 16 <= (size_t)kProgChunkBytes;
+            };
+            while (k < ps.iend && P.prog_instrs[k].op != OP_DENSE1 && P.prog_instrs[k].op != OP_DENSE2 &&
+                   pairs.size() + 32 < kMaxFactors && (k == r0 || fits_one_more())) {
+                const Instr &d = P.prog_instrs[k];
+                if (d.op == OP_DIAG1 || d.op == OP_DIAG2)
+                    touched |= 1u << d.p0;
+                if (d.op == OP_DIAG2)
+                    touched |= 1u << d.p1;
                 if (d.op == OP_DIAG1 || d.op == OP_DIAG2) {
                     G *= cplx(d.gate, 0);
                     alpha[d.p0] *= cplx(d.gate, 1);
@@ -609,7 +676,7 @@ static void compile_programs(PlanHost &P)
             uint8_t cnt[8] = {0};
             for (auto &f : facs)
                 cnt[f.first.kind]++;
-            reserve(32 + facs.size() * fsz + 16);
+            reserve(32 + facs.size() * fsz + (size_t)(k - r0) * esz + 16);
             RecHdr h;
             std::memset(&h, 0, sizeof(h));
             h.type = REC_RUN;
@@ -618,7 +685,7 @@ static void compile_programs(PlanHost &P)
             h.c = cnt[FAC_C_FIXED];
             h.d = cnt[FAC_C_MIXED];
             h.e = cnt[FAC_C_SLOTS];
-            h.site = P.instrs[r0].site;
+            h.site = P.prog_instrs[r0].site;
             h.ibeg = r0;
             h.iend = k;
             put(&h, 16);
@@ -631,6 +698,25 @@ static void compile_programs(PlanHost &P)
                 putc(f.second);
             }
             pad16();
+            // the run gate by gate, for nodes with a Pauli inside it (see GateEnt)
+            for (uint32_t x = r0; x < k; x++) {
+                const Instr &d = P.prog_instrs[x];
+                GateEnt g;
+                std::memset(&g, 0, sizeof(g));
+                g.op = d.op;
+                g.fl = (uint8_t)d.pad;
+                g.j0 = d.j0;
+                g.p0 = d.p0;
+                g.j1 = d.j1;
+                g.p1 = d.p1;
+                g.np0 = d.np0;
+                g.np1 = d.np1;
+                g.npaulis = d.npaulis;
+                g.site = d.site;
+                put(&g, 16);
+                for (int e = 0; e < 4; e++)
+                    putc(d.op == OP_DIAG1 || d.op == OP_DIAG2 ? cplx(d.gate, e) : std::complex<double>(1.0, 0.0));
+            }
         }
         ps.chunk_end = (uint32_t)P.chunk_off.size();
     }
@@ -864,6 +950,7 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
         if (S.rank_q[r] != r)
             return "internal: sampler layout invariant broken";
     P.fuse = (o.flags & TQS_FLAG_FUSE) != 0;
+    sink_diagonals(P);
     compile_programs(P);
     return "";
 }

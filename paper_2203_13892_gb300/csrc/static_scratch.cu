@@ -124,6 +124,9 @@ extern "C" tqs_status tqs_simulate_static(const tqs_circuit *c, const tqs_noise 
     // kernels before it is read; the histogram is zeroed by execute)
     cudaError_t e = cudaMemcpyAsync(dp.d_instr, H.instrs.data(), sizeof(tqs::Instr) * H.instrs.size(),
                                     cudaMemcpyHostToDevice, dp.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dp.d_pinstr, H.prog_instrs.data(), sizeof(tqs::Instr) * H.prog_instrs.size(),
+                            cudaMemcpyHostToDevice, dp.stream);
     if (e == cudaSuccess) {
         if (H.prec == TQS_FP64)
             e = cudaMemcpyAsync(dp.d_mats, H.mats64.data(), 8 * H.mats64.size(), cudaMemcpyHostToDevice, dp.stream);
