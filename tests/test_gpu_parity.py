@@ -85,7 +85,8 @@ def test_node_amplitudes(orc, prec, tol, tile):
 
 
 @pytest.mark.parametrize("circ_fn,tile", [(lambda: qft(12), 7), (lambda: random_layers(11, 9, 4), 6),
-                                          (lambda: mixed_circuit(10, 8), 12), (lambda: ghz(12), 5 + 1)])
+                                          (lambda: mixed_circuit(10, 8), 12), (lambda: ghz(12), 5 + 1),
+                                          (lambda: qft(14), 10), (lambda: mixed_circuit(12, 6), 11)])
 def test_tree_counts_fp64_bit_exact(orc, circ_fn, tile):
     circ = circ_fn()
     shots, seed = 3000, 4
