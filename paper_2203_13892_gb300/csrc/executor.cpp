@@ -194,13 +194,14 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
         CK(cudaMemcpyAsync(d_mats, H.mats64.data(), 8 * H.mats64.size(), cudaMemcpyHostToDevice, stream));
     else
         CK(cudaMemcpyAsync(d_mats, H.mats32.data(), 4 * H.mats32.size(), cudaMemcpyHostToDevice, stream));
-    // per level: pass start sites (npass + 1 entries), concatenated
+    // per level: where each pass starts in the level's instruction table (which
+    // runs in pass order; npass + 1 entries), concatenated
     pst_host.clear();
     pst_off.clear();
     for (auto &lv : H.levels) {
         pst_off.push_back((uint32_t)pst_host.size());
         for (uint32_t p = lv.pass_begin; p < lv.pass_end; p++)
-            pst_host.push_back(H.passes[p].site_begin);
+            pst_host.push_back(H.passes[p].ibeg - H.passes[lv.pass_begin].ibeg);
         pst_host.push_back(lv.g1 - lv.g0);
     }
     CK(cudaMemcpyAsync(d_pass_start, pst_host.data(), 4 * pst_host.size(), cudaMemcpyHostToDevice, stream));

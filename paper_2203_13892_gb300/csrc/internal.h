@@ -116,7 +116,7 @@ struct Pass {
     uint32_t ibeg, iend;          // instruction range (global instruction list)
     uint32_t chunk_begin, chunk_end;  // program chunks (offsets in PlanHost::chunk_off)
     uint32_t fused_blocks;        // REC_FUSED records in the program
-    uint32_t site_begin;          // first site of the pass, relative to the level
+    uint32_t site_begin;          // first (lowest) site of the pass, relative to the level
     uint32_t t, L;                // tile width and number of contiguous low bits
     uint8_t tbits[kMaxTile];      // physical bit of each tile position (ascending)
     uint8_t hbits[32];            // remaining physical bits (ascending), n - t of them
@@ -188,7 +188,8 @@ struct DevTables {
 struct NoiseLaunch {
     const Instr *instr;        // the level's instructions (one per site, in order)
     uint32_t sites;            // sites in the level
-    const uint32_t *pass_start;// device: level-relative first site of each pass, npass+1 entries
+    const uint32_t *pass_start;// device: first table entry of each pass (the level's instruction
+                               // table runs in pass order), npass+1 entries
     uint32_t npass;
     uint64_t node_lo, nnodes;  // global ids [node_lo, node_lo + nnodes)
     const NodeMeta *parent_meta;  // nullptr for level 0

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256) noise_kernel(const __grid_constant__ Nois
                 if (wb == 1 || wb == 2) xm ^= 1u << I.np1;
                 if (wb == 2) yc++;
             }
-            nout[s] = (uint8_t)pz;
+            nout[I.site] = (uint8_t)pz;  // the table runs in pass order; the noise row is by site
         }
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) noise_kernel(const __grid_constant__ Nois
             }
         }
         if (s < a.sites) {
-            // boundary p (1..npass) sits after site pass_start[p]-1
+            // boundary p (1..npass) sits after table entry pass_start[p]-1
             for (uint32_t p = 1; p <= a.npass; p++)
                 if (a.pass_start[p] == s + 1)
                     mout[p] = NodeMeta{mask ^ xm, (phase + yc) & 3u};

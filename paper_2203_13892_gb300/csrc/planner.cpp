@@ -845,36 +845,59 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
         lv.perm = perm_after[lv.g1];
     }
 
-    // tile passes per level (greedy: grow the set of qubits that dense gates need
-    // until it no longer fits a tile)
+    // tile passes per level, by list scheduling: a pass takes, in gate order,
+    // every gate whose qubits no earlier untaken gate touches and whose dense
+    // qubits still fit the tile (diagonal gates and lazy SWAP noise sites fit
+    // any tile).  Gates that share a (physical) qubit keep their order, so each
+    // gate and the Pauli drawn after it act between the same neighbours as in
+    // the circuit; gates on disjoint qubits commute.  A pass can thus run ahead
+    // on the qubits it holds instead of stopping at the first gate that does
+    // not fit.
+    auto gate_qubits = [&](uint32_t g) {
+        const bool two = is_two_qubit(c.gates[g].kind);
+        uint32_t q = (1u << low[g].np0) | (two ? (1u << low[g].np1) : 0u);
+        if (op[g] != OP_NOP)
+            q |= (1u << low[g].p0) | (two ? (1u << low[g].p1) : 0u);
+        return q;
+    };
     for (uint32_t i = 0; i < L; i++) {
         Level &lv = P.levels[i];
         lv.pass_begin = (uint32_t)P.passes.size();
-        uint32_t g = lv.g0;
+        std::vector<uint32_t> rem;
+        for (uint32_t g = lv.g0; g < lv.g1; g++)
+            rem.push_back(g);
         do {
-            uint32_t need = 0, start = g;
-            uint32_t lowbits = (1u << std::min<uint32_t>(n, 4)) - 1;
-            for (; g < lv.g1; g++) {
+            uint32_t need = 0, blocked = 0;
+            const uint32_t lowbits = (1u << std::min<uint32_t>(n, 4)) - 1;
+            std::vector<uint32_t> take, left;
+            for (uint32_t g : rem) {
+                const uint32_t q = gate_qubits(g);
                 uint32_t add = 0;
                 if (op[g] == OP_DENSE1)
                     add = 1u << low[g].p0;
                 else if (op[g] == OP_DENSE2)
                     add = (1u << low[g].p0) | (1u << low[g].p1);
-                if ((uint32_t)__builtin_popcount(need | add | lowbits) > std::min(n, tmax))
-                    break;
+                if ((q & blocked) || (uint32_t)__builtin_popcount(need | add | lowbits) > std::min(n, tmax)) {
+                    blocked |= q;
+                    left.push_back(g);
+                    continue;
+                }
                 need |= add;
+                take.push_back(g);
             }
+            if (take.empty() && !rem.empty())
+                return "internal: pass scheduling made no progress";  // an empty level gets one empty pass
             Pass ps;
             std::memset(&ps, 0, sizeof(ps));
             ps.level = i;
-            ps.site_begin = start - lv.g0;
+            ps.site_begin = take.empty() ? 0u : take[0] - lv.g0;
             choose_tile(n, tmax, need, nullptr, 0, ps);
             ps.ibeg = (uint32_t)P.instrs.size();
             uint8_t pos[32];
             std::memset(pos, 0xff, sizeof(pos));
             for (uint32_t j = 0; j < ps.t; j++)
                 pos[ps.tbits[j]] = (uint8_t)j;
-            for (uint32_t k = start; k < g; k++) {
+            for (uint32_t k : take) {
                 Instr in;
                 std::memset(&in, 0, sizeof(in));
                 in.op = op[k];
@@ -892,7 +915,8 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
             }
             ps.iend = (uint32_t)P.instrs.size();
             P.passes.push_back(ps);
-        } while (g < lv.g1);
+            rem.swap(left);
+        } while (!rem.empty());
         lv.pass_end = (uint32_t)P.passes.size();
     }
 

@@ -136,7 +136,7 @@ extern "C" tqs_status tqs_simulate_static(const tqs_circuit *c, const tqs_noise 
     for (const auto &lv : H.levels) {
         dp.pst_off.push_back((uint32_t)dp.pst_host.size());
         for (uint32_t p = lv.pass_begin; p < lv.pass_end; p++)
-            dp.pst_host.push_back(H.passes[p].site_begin);
+            dp.pst_host.push_back(H.passes[p].ibeg - H.passes[lv.pass_begin].ibeg);
         dp.pst_host.push_back(lv.g1 - lv.g0);
     }
     if (e == cudaSuccess)
