@@ -585,7 +585,7 @@ template <typename C> __device__ __forceinline__ C shfl_xor_c(C a, int m)
 }
 
 #ifndef TQS_FP32_MIN_CTAS
-#define TQS_FP32_MIN_CTAS 2  // resident CTAs per SM asked of ptxas for FP32 tiles of 2^12 amplitudes
+#define TQS_FP32_MIN_CTAS 3  // resident CTAs per SM asked of ptxas for FP32 tiles of 2^12 amplitudes
 #endif
 // FUSE: the pass holds REC_FUSED records (FP32 tiles of 2^11 or 2^12 only); a
 // separate instantiation so that the tensor-core code does not weigh on the
