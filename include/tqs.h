@@ -265,6 +265,17 @@ tqs_status tqs_debug_node_state(const tqs_circuit *c, const tqs_noise *nz, uint6
 tqs_status tqs_debug_node_noise(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots,
                                 uint64_t seed, const tqs_options *opts, uint32_t level,
                                 uint64_t node, uint8_t *paulis_out);
+/* tqs_debug_plan_order (host only, no device call): the order in which the plan
+ * applies the circuit's gates.  order_out[i] (HOST, n_gates entries) = the gate
+ * index applied i-th (levels in turn, each level's passes in turn, each pass in
+ * its program order); pass_out[i] = the global pass that applies it; tile_out
+ * (optional, one entry per pass) = the pass's tile as a mask of physical qubits
+ * (SWAPs are a relabelling: physical = where a logical qubit lives at that
+ * point); *npasses_out = the number of passes.  Gates that share a physical
+ * qubit appear in circuit order. */
+tqs_status tqs_debug_plan_order(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots,
+                                const tqs_options *opts, uint32_t *order_out, uint32_t *pass_out,
+                                uint32_t *tile_out, uint32_t *npasses_out);
 
 /* Simulation without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory, such as

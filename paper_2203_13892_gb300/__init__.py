@@ -20,6 +20,7 @@ from .capi import (  # noqa: F401
     tqs_circuit_create,
     tqs_circuit_destroy,
     tqs_debug_node_noise,
+    tqs_debug_plan_order,
     tqs_debug_node_state,
     tqs_last_error,
     tqs_learned_candidate,

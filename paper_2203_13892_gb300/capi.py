@@ -88,7 +88,8 @@ EXPORTS = (
     "tqs_circuit_create", "tqs_circuit_destroy", "tqs_noise_model", "tqs_noise_destroy",
     "tqs_options_default", "tqs_partition", "tqs_simulate", "tqs_plan_create",
     "tqs_plan_execute", "tqs_plan_workspace_bytes", "tqs_plan_destroy",
-    "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_simulate_static", "tqs_last_error",
+    "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_debug_plan_order", "tqs_simulate_static",
+    "tqs_last_error",
     "tqs_abi_version", "tqs_batch_create", "tqs_batch_execute", "tqs_batch_counts",
     "tqs_batch_device_counts", "tqs_batch_size", "tqs_batch_destroy", "tqs_learned_param_count",
     "tqs_learned_features", "tqs_learned_candidate", "tqs_learned_train", "tqs_learned_loss_grad",
@@ -135,6 +136,9 @@ def lib():
             L.tqs_debug_node_noise.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.POINTER(tqs_options),
                                                C.c_uint32, C.c_uint64, C.POINTER(C.c_uint8)]
             L.tqs_debug_node_noise.restype = st
+            u32p = C.POINTER(C.c_uint32)
+            L.tqs_debug_plan_order.argtypes = [vp, vp, C.c_uint64, C.POINTER(tqs_options), u32p, u32p, u32p, u32p]
+            L.tqs_debug_plan_order.restype = st
             L.tqs_simulate_static.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.POINTER(tqs_options), vp]
             L.tqs_simulate_static.restype = st
             L.tqs_batch_create.argtypes = [C.c_size_t, C.POINTER(vp), C.POINTER(vp), u64p, C.POINTER(tqs_options),
@@ -334,6 +338,21 @@ def tqs_debug_node_noise(c: Handle, nz: Handle, shots: int, seed: int, opts: Opt
     _check(lib().tqs_debug_node_noise(c.ptr, nz.ptr, int(shots), int(seed), C.byref(opts) if opts else None,
                                       int(level), int(node), out.ctypes.data_as(C.POINTER(C.c_uint8))))
     return out[:sites]
+
+
+def tqs_debug_plan_order(c: Handle, nz: Handle, shots: int, opts: Optional[tqs_options], n_gates: int):
+    """Host only.  Returns (order, pass_of, tiles): the gate indices in the order
+    the plan applies them, the pass applying each, and each pass's tile (mask of
+    physical qubits)."""
+    order = np.zeros(max(n_gates, 1), dtype=np.uint32)
+    pas = np.zeros(max(n_gates, 1), dtype=np.uint32)
+    tiles = np.zeros(max(n_gates, 1) + 64, dtype=np.uint32)
+    npass = C.c_uint32()
+    u32p = C.POINTER(C.c_uint32)
+    _check(lib().tqs_debug_plan_order(c.ptr, nz.ptr, int(shots), C.byref(opts) if opts else None,
+                                      order.ctypes.data_as(u32p), pas.ctypes.data_as(u32p),
+                                      tiles.ctypes.data_as(u32p), C.byref(npass)))
+    return order[:n_gates], pas[:n_gates], tiles[:npass.value]
 
 
 def tqs_simulate_static(c: Handle, nz: Handle, shots: int, seed: int, opts: Optional[tqs_options],

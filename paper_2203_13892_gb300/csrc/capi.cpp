@@ -224,6 +224,41 @@ tqs_status tqs_partition(const tqs_circuit *c, const tqs_noise *nz, uint64_t sho
     return TQS_OK;
 }
 
+tqs_status tqs_debug_plan_order(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
+                                uint32_t *order_out, uint32_t *pass_out, uint32_t *tile_out, uint32_t *npasses_out)
+{
+    if (!c || !nz || !order_out || !pass_out || !npasses_out)
+        return fail(TQS_EINVAL, "NULL argument");
+    if (shots == 0)
+        return fail(TQS_EINVAL, "shots must be >= 1");
+    tqs_options o = opts_or_default(opts);
+    std::vector<uint64_t> arity;
+    std::vector<uint32_t> split;
+    tqs_status st = from_msg(tqs::partition(c->c, nz->nz, shots, o, arity, split));
+    if (st != TQS_OK)
+        return st;
+    tqs::PlanHost H;
+    st = from_msg(tqs::build_plan(c->c, nz->nz, shots, o, arity, split, H));
+    if (st != TQS_OK)
+        return st;
+    size_t k = 0;
+    for (uint32_t q = 0; q < (uint32_t)H.passes.size(); q++) {
+        const tqs::Pass &ps = H.passes[q];
+        for (uint32_t i = ps.ibeg; i < ps.iend; i++, k++) {
+            order_out[k] = H.prog_instrs[i].gate;
+            pass_out[k] = q;
+        }
+        if (tile_out) {
+            uint32_t m = 0;
+            for (uint32_t j = 0; j < ps.t; j++)
+                m |= 1u << ps.tbits[j];
+            tile_out[q] = m;
+        }
+    }
+    *npasses_out = (uint32_t)H.passes.size();
+    return TQS_OK;
+}
+
 tqs_status tqs_plan_create(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
                            tqs_plan **out)
 {
