@@ -223,7 +223,7 @@ void tqs_batch_destroy(tqs_batch *b);
  * chooses between candidate trees; class = 10*mode + k means k extra levels with
  * DCP's first-level sample-size rule (Sec. 3.2, Eq. sample_size_formula) and
  * equal lower arities, cut into equal parts (mode 0) or with every cut moved to
- * the nearest tile-pass boundary (mode 1).  DCP is the fallback and the judge: a
+ * the nearest tile-pass boundary (mode 1).  DCP is the fallback and the arbiter: a
  * class is allowed only when its first-level arity A_0 is at least DCP's (no
  * wider Hoeffding bound on A_0) and it has no more levels than DCP; with no model
  * loaded, TQS_PART_LEARNED returns TQS_EUNSUPPORTED.

@@ -1,6 +1,6 @@
 // learned.cpp -- the learned partitioner: circuit features, the candidate trees
 // it chooses between, and the partition step that consults the network with DCP
-// as the fallback and the judge (Sec. 3.2's DCP stays the reference).
+// as the fallback and the arbiter (Sec. 3.2's DCP stays the reference).
 //
 // A candidate is class = 10 * mode + k: k extra levels (k + 1 subcircuits) with
 // the first-level arity from DCP's sample-size rule for that k, equal arities

@@ -5,7 +5,7 @@ Data: for each random layered circuit the simulator times every candidate tree
 that DCP allows (tqs_learned_features' `allowed` mask) on a few whole level-0
 subtrees, and the label is the fastest.  Training runs the library's own GPU
 kernels (tqs_learned_train).  At run time TQS_PART_LEARNED consults the loaded
-model and keeps DCP as the fallback and the judge.
+model and keeps DCP as the fallback and the arbiter.
 
     python -m paper_2203_13892_gb300.learned generate --count 5000 --out data.npz
     python -m paper_2203_13892_gb300.learned train --data data.npz --out model.npz

@@ -1,5 +1,5 @@
 """The learned partitioner's GPU kernels against the FP64 oracle network, its
-training, and its use inside the partition step with DCP as fallback/judge."""
+training, and its use inside the partition step with DCP as fallback and arbiter."""
 import numpy as np
 import pytest
 
