@@ -66,7 +66,7 @@ def load_peaks():
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in sorted(os.listdir(os.path.join(ROOT, "paper_2203_13892_gb300", "csrc"))):
-        if f.endswith((".cu", ".h")):
+        if f.endswith((".cu", ".cuh", ".h")):
             h.update(open(os.path.join(ROOT, "paper_2203_13892_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

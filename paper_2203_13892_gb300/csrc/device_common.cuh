@@ -1,0 +1,59 @@
+// device_common.cuh -- device helpers shared by the kernels of libtqs: the
+// counter-based Philox4x32-10 generator and complex arithmetic.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace tqs {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32
+// multiply-xor S-box with the Weyl key schedule.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t id, uint32_t index, uint32_t dom)
+{
+    return philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), index, dom),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// ---------------------------------------------------------------------------
+// Complex helpers
+// ---------------------------------------------------------------------------
+template <typename R> struct CT;
+template <> struct CT<float> { using T = float2; };
+template <> struct CT<double> { using T = double2; };
+
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b)
+{
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cmadd(C a, C b, C acc)  // acc + a*b
+{
+    return mk(acc.x + a.x * b.x - a.y * b.y, acc.y + a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cneg(C a) { return mk(-a.x, -a.y); }
+template <typename R> __device__ __forceinline__ R norm2(typename CT<R>::T a)
+{
+    return a.x * a.x + a.y * a.y;
+}
+
+
+}  // namespace tqs
