@@ -114,6 +114,23 @@ def test_explicit_trees_fp64_bit_exact(orc, arity, split_fn):
     assert np.array_equal(counts, want)
 
 
+@pytest.mark.parametrize("idx", range(6))
+def test_speed_accuracy_study_trees_fp64_bit_exact(orc, idx):
+    """The six tree structures of the speed-against-accuracy study (Sec. 5.6:
+    DCP, XCP (20,10,5), UCP (10,10,10), (5,10,20), (2,2,250) and (250,1,1)) on
+    its phase-estimation workload: FP64 counts bit-exact for two seeds, so the
+    study's fidelities are the oracle's."""
+    from paper_2203_13892_gb300 import sweep
+
+    circ = sweep.workload()
+    label, arity, split, shots = sweep.structures(circ)[idx]
+    for seed in (0, 7):
+        counts, F, rep = run(circ, shots, seed, prec="fp64", arity=arity, split=split)
+        want = orc.core.run_tree(circ, P1, P2, PM, shots, seed, arity, split)
+        assert rep["arity"] == arity and int(counts.sum()) == shots
+        assert np.array_equal(counts, want), (label, seed)
+
+
 def test_degenerate_tree_equals_baseline_on_gpu():
     circ = random_layers(10, 6, 1)
     G = len(circ.gates)

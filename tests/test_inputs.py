@@ -3,7 +3,7 @@ circuits and the determinism of the seeded generators."""
 import os
 
 from tqs_inputs import (batch_circuits_spec, qft, random_layers, read_text, write_text,
-                        inverse_qft_on_fourier_state, splitmix64)
+                        inverse_qft_on_fourier_state, qpe, splitmix64)
 
 
 def test_qft_gate_counts():
@@ -12,6 +12,15 @@ def test_qft_gate_counts():
         n1, n2 = c.counts()
         assert n1 == n and n2 == n * (n - 1) // 2 + n // 2
     assert len(qft(20)) == 220
+
+
+def test_qpe_gate_counts():
+    for m in (4, 8):
+        c = qpe(m, 0.3)
+        assert c.n == m + 1
+        # X, m H, m controlled powers, m(m-1)/2 CP + m H (inverse QFT), m/2 SWAP
+        assert len(c) == 1 + 3 * m + m * (m - 1) // 2 + m // 2
+    assert len(qpe(8, 0.3)) == 57
 
 
 def test_random_layer_counts_and_determinism():

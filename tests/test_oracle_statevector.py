@@ -7,7 +7,7 @@ import math
 import numpy as np
 import pytest
 
-from tqs_inputs import Circuit, ghz, qft_on_basis, inverse_qft_on_fourier_state, random_layers
+from tqs_inputs import Circuit, ghz, qft_on_basis, inverse_qft_on_fourier_state, qpe, random_layers
 
 I2 = np.eye(2)
 
@@ -104,6 +104,22 @@ def test_inverse_qft_on_fourier_state_returns_basis(orc, n, b):
     psi = orc.core.ideal_state(inverse_qft_on_fourier_state(n, b))
     assert abs(abs(psi[b]) - 1.0) < 1e-12
     assert np.sum(np.abs(psi) ** 2) - abs(psi[b]) ** 2 < 1e-20 + 1e-12
+
+
+@pytest.mark.parametrize("m,phi", [(4, 0.3), (6, 1.0 / 3.0), (8, 0.3), (5, 5.0 / 32.0)])
+def test_qpe_textbook_distribution(orc, m, phi):
+    """Phase estimation with m counting qubits: the target stays in |1> and the
+    counting register reads y with probability
+    |2^-m sum_k exp(2 pi i k (phi - y/2^m))|^2 = sin^2(pi 2^m d) / (2^2m sin^2(pi d)),
+    d = phi - y/2^m (exactly 1 at y = phi 2^m when that is an integer)."""
+    M_ = 1 << m
+    psi = orc.core.ideal_state(qpe(m, phi))
+    p = np.abs(psi) ** 2
+    assert p[:M_].sum() < 1e-24 + 1e-14  # target qubit m is 1 throughout
+    d = phi - np.arange(M_) / M_
+    s = np.sin(np.pi * d)
+    want = np.where(np.abs(s) < 1e-12, 1.0, np.sin(np.pi * M_ * d) ** 2 / np.where(np.abs(s) < 1e-12, 1.0, M_ * M_ * s * s))
+    assert np.max(np.abs(p[M_:] - want)) < 1e-12
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])

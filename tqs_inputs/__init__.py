@@ -19,6 +19,7 @@ from .circuits import (  # noqa: F401
     qft,
     qft_on_basis,
     inverse_qft_on_fourier_state,
+    qpe,
     random_layers,
     ghz,
     batch_circuits_spec,

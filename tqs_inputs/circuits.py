@@ -1,4 +1,4 @@
-"""Circuit generators for the synthetic workloads (QFT, random layers, GHZ).
+"""Circuit generators for the synthetic workloads (QFT, random layers, GHZ, QPE).
 
 The paper's 48 benchmark circuits are not available; these generators stand in
 for the *shape* of its QFT and random-circuit (QV/QSC-like) classes
@@ -99,6 +99,32 @@ def inverse_qft_on_fourier_state(n: int, b: int) -> Circuit:
     for q in range(n // 2):
         c.add("swap", q, n - 1 - q)
     for j in range(n):
+        for k in range(j):
+            c.add("cp", k, j, -math.pi / (1 << (j - k)))
+        c.add("h", j)
+    return c
+
+
+def qpe(m: int, phi: float) -> Circuit:
+    """Textbook phase estimation with m counting qubits (0..m-1) and one target
+    qubit m prepared in |1>, the eigenstate of the phase gate P(2 pi phi):
+    X on the target, H on every counting qubit, a controlled P(2 pi phi)^(2^q)
+    from counting qubit q (one CP of angle 2 pi phi 2^q), then the inverse QFT
+    of the counting register (the same swaps and gate order as
+    inverse_qft_on_fourier_state).  The counting register ends near
+    |round(phi 2^m)>; for phi not a multiple of 2^-m its outcome distribution is
+    a narrow peak of width ~1 around phi 2^m.  m = 8 gives a 9-qubit circuit of
+    57 gates (8 + 1 one-qubit H/X, 8 CP for the controlled powers, 28 CP and 8 H
+    for the inverse QFT, 4 SWAP)."""
+    c = Circuit(m + 1, name=f"qpe{m + 1}")
+    c.add("x", m)
+    for q in range(m):
+        c.add("h", q)
+    for q in range(m):
+        c.add("cp", q, m, math.remainder(2.0 * math.pi * phi * float(1 << q), 2.0 * math.pi))
+    for q in range(m // 2):
+        c.add("swap", q, m - 1 - q)
+    for j in range(m):
         for k in range(j):
             c.add("cp", k, j, -math.pi / (1 << (j - k)))
         c.add("h", j)
