@@ -3,7 +3,7 @@ circuits and the determinism of the seeded generators."""
 import os
 
 from tqs_inputs import (batch_circuits_spec, qft, random_layers, read_text, write_text,
-                        inverse_qft_on_fourier_state, qpe, splitmix64)
+                        inverse_qft_on_fourier_state, qaoa_maxcut, qpe, random_regular_graph, splitmix64)
 
 
 def test_qft_gate_counts():
@@ -21,6 +21,22 @@ def test_qpe_gate_counts():
         # X, m H, m controlled powers, m(m-1)/2 CP + m H (inverse QFT), m/2 SWAP
         assert len(c) == 1 + 3 * m + m * (m - 1) // 2 + m // 2
     assert len(qpe(8, 0.3)) == 57
+
+
+def test_random_regular_graph_and_qaoa_counts():
+    for n, d, seed in [(16, 3, 7), (10, 3, 5), (9, 4, 2)]:
+        E = random_regular_graph(n, d, seed)
+        assert E == random_regular_graph(n, d, seed)
+        assert len(E) == n * d // 2 and len(set(E)) == len(E)
+        assert all(0 <= u < v < n for u, v in E)
+        deg = [0] * n
+        for u, v in E:
+            deg[u] += 1
+            deg[v] += 1
+        assert deg == [d] * n
+    E = random_regular_graph(16, 3, 7)
+    c = qaoa_maxcut(16, E, 0.4, 0.3)
+    assert len(c) == 16 + 3 * len(E) + 16 and c.counts() == (16 + len(E) + 16, 2 * len(E))
 
 
 def test_random_layer_counts_and_determinism():

@@ -7,7 +7,8 @@ import math
 import numpy as np
 import pytest
 
-from tqs_inputs import Circuit, ghz, qft_on_basis, inverse_qft_on_fourier_state, qpe, random_layers
+from tqs_inputs import (Circuit, ghz, qft_on_basis, inverse_qft_on_fourier_state, qaoa_maxcut, qpe,
+                        random_layers, random_regular_graph)
 
 I2 = np.eye(2)
 
@@ -120,6 +121,33 @@ def test_qpe_textbook_distribution(orc, m, phi):
     s = np.sin(np.pi * d)
     want = np.where(np.abs(s) < 1e-12, 1.0, np.sin(np.pi * M_ * d) ** 2 / np.where(np.abs(s) < 1e-12, 1.0, M_ * M_ * s * s))
     assert np.max(np.abs(p[M_:] - want)) < 1e-12
+
+
+@pytest.mark.parametrize("n,d,gseed", [(10, 3, 5), (8, 3, 11), (9, 4, 2)])
+def test_qaoa_p1_maxcut_closed_form(orc, n, d, gseed):
+    """One QAOA layer for MaxCut: the expected cut has the closed form of Wang,
+    Hadfield, Jiang and Rieffel (Phys. Rev. A 97, 022304, 2018) for any graph,
+    per edge uv with D_u = deg(u) - 1, D_v = deg(v) - 1 and t_uv triangles on uv:
+    1/2 + sin(4b) sin(g) (cos^D_u g + cos^D_v g) / 4
+        - sin^2(2b) cos^(D_u + D_v - 2 t_uv) g (1 - cos^t_uv 2g) / 4.
+    It pins the oracle's H, CX, RZ and RX and the generator's decomposition."""
+    E = random_regular_graph(n, d, gseed)
+    nb = {v: set() for v in range(n)}
+    for u, v in E:
+        nb[u].add(v)
+        nb[v].add(u)
+    x = np.arange(1 << n)
+    cut = np.zeros(1 << n)
+    for u, v in E:
+        cut += ((x >> u) & 1) != ((x >> v) & 1)
+    for g, b in [(0.3, 0.2), (1.1, 0.7), (2.5, 1.3), (0.7, -0.4)]:
+        want = 0.0
+        for u, v in E:
+            du, dv, t = len(nb[u]) - 1, len(nb[v]) - 1, len(nb[u] & nb[v])
+            want += (0.5 + 0.25 * math.sin(4 * b) * math.sin(g) * (math.cos(g) ** du + math.cos(g) ** dv)
+                     - 0.25 * math.sin(2 * b) ** 2 * math.cos(g) ** (du + dv - 2 * t) * (1 - math.cos(2 * g) ** t))
+        p = np.abs(orc.core.ideal_state(qaoa_maxcut(n, E, g, b))) ** 2
+        assert abs(float(p @ cut) - want) < 1e-11, (g, b)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])

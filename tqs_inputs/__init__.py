@@ -20,6 +20,8 @@ from .circuits import (  # noqa: F401
     qft_on_basis,
     inverse_qft_on_fourier_state,
     qpe,
+    qaoa_maxcut,
+    random_regular_graph,
     random_layers,
     ghz,
     batch_circuits_spec,

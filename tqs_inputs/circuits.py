@@ -1,4 +1,4 @@
-"""Circuit generators for the synthetic workloads (QFT, random layers, GHZ, QPE).
+"""Circuit generators for the synthetic workloads (QFT, random layers, GHZ, QPE, QAOA).
 
 The paper's 48 benchmark circuits are not available; these generators stand in
 for the *shape* of its QFT and random-circuit (QV/QSC-like) classes
@@ -149,6 +149,48 @@ def random_layers(n: int, layers: int, seed: int) -> Circuit:
             perm[i], perm[j] = perm[j], perm[i]
         for i in range(n // 2):
             c.add("cz", perm[2 * i], perm[2 * i + 1])
+    return c
+
+
+def random_regular_graph(n: int, d: int, seed: int) -> List[Tuple[int, int]]:
+    """A random simple d-regular graph on n vertices (n*d even) by the pairing
+    model: n*d half-edges are shuffled (Fisher-Yates, SplitMix64(seed)) and paired
+    consecutively; a pairing with a loop or a repeated edge is drawn again.
+    Edges as (u, v) with u < v, sorted."""
+    if (n * d) % 2 or d >= n:
+        raise ValueError("need n*d even and d < n")
+    rng = splitmix64(seed)
+    while True:
+        stubs = [v for v in range(n) for _ in range(d)]
+        for i in range(len(stubs) - 1, 0, -1):
+            j = rng.below(i + 1)
+            stubs[i], stubs[j] = stubs[j], stubs[i]
+        edges = set()
+        ok = True
+        for i in range(0, len(stubs), 2):
+            u, v = sorted((stubs[i], stubs[i + 1]))
+            if u == v or (u, v) in edges:
+                ok = False
+                break
+            edges.add((u, v))
+        if ok:
+            return sorted(edges)
+
+
+def qaoa_maxcut(n: int, edges: List[Tuple[int, int]], gamma: float, beta: float) -> Circuit:
+    """One QAOA layer for MaxCut (cost C = sum over edges of (1 - Z_u Z_v)/2):
+    H on every qubit, then exp(-i gamma C) edge by edge as CX(u,v) RZ_v(-gamma)
+    CX(u,v) (exp(+i gamma Z_u Z_v / 2), the global phase dropped), then the mixer
+    exp(-i beta sum_q X_q) as RX(2 beta) on every qubit.  n + 3|E| + n gates."""
+    c = Circuit(n, name=f"qaoa{n}_g{gamma:.4f}_b{beta:.4f}")
+    for q in range(n):
+        c.add("h", q)
+    for u, v in edges:
+        c.add("cx", u, v)
+        c.add("rz", v, -1, -gamma)
+        c.add("cx", u, v)
+    for q in range(n):
+        c.add("rx", q, -1, 2.0 * beta)
     return c
 
 
