@@ -108,6 +108,14 @@ typedef enum {
                                      gates on t - 7 tile qubits as one fused 3xTF32 product on the tensor
                                      cores (off by default: on circuits whose blocks hold only a few gates
                                      the per-gate path is faster) */
+#define TQS_FLAG_HOST_POOL 0x10u  /* keep every level's state slots in pinned host memory mapped into the
+                                     device's address space, read and written in place by the kernels
+                                     (Sec. 3.3-3.4: idle host memory holds the intermediate states; on a
+                                     Grace-Blackwell node the accesses go over NVLink-C2C).  Without this
+                                     flag, a plan whose library-allocated workspace cannot hold one node
+                                     per level moves the upper levels' slots there by itself.  At most a
+                                     quarter of the host's physical memory is pinned (the node batch
+                                     shrinks to fit); ignored by tqs_simulate_static. */
 
 /* Kernel classes timed under TQS_FLAG_PROFILE (index into report.prof_*). */
 #define TQS_PROF_NOISE 0   /* Philox noise draws + Pauli frames */
@@ -197,6 +205,9 @@ tqs_status tqs_plan_create(const tqs_circuit *c, const tqs_noise *nz, uint64_t s
                            const tqs_options *opts, tqs_plan **out);
 tqs_status tqs_plan_execute(tqs_plan *p, uint64_t seed, uint64_t *d_counts, tqs_report *report);
 size_t tqs_plan_workspace_bytes(const tqs_plan *p);
+/* Bytes of the plan's state pool held in mapped host memory (0 when all of it
+ * is in device memory; see TQS_FLAG_HOST_POOL). */
+size_t tqs_plan_host_pool_bytes(const tqs_plan *p);
 void tqs_plan_destroy(tqs_plan *p);
 
 /* Batched execution (many independent simulations, uneven sizes).  All

@@ -37,6 +37,7 @@ from .capi import (  # noqa: F401
     tqs_plan_create,
     tqs_plan_destroy,
     tqs_plan_execute,
+    tqs_plan_host_pool_bytes,
     tqs_plan_workspace_bytes,
     tqs_simulate,
     tqs_simulate_static,

@@ -24,6 +24,7 @@ TQS_FLAG_NO_FIDELITY = 0x1
 TQS_FLAG_PROFILE = 0x2
 TQS_FLAG_AUTOTUNE = 0x4
 TQS_FLAG_FUSE = 0x8
+TQS_FLAG_HOST_POOL = 0x10
 TQS_MAX_LEVELS = 17
 TQS_PROF_KINDS = 4
 PROF_NAMES = ("noise", "store", "sums", "sample")
@@ -87,7 +88,7 @@ _lib = None
 EXPORTS = (
     "tqs_circuit_create", "tqs_circuit_destroy", "tqs_noise_model", "tqs_noise_destroy",
     "tqs_options_default", "tqs_partition", "tqs_simulate", "tqs_plan_create",
-    "tqs_plan_execute", "tqs_plan_workspace_bytes", "tqs_plan_destroy",
+    "tqs_plan_execute", "tqs_plan_workspace_bytes", "tqs_plan_host_pool_bytes", "tqs_plan_destroy",
     "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_debug_plan_order", "tqs_simulate_static",
     "tqs_last_error",
     "tqs_abi_version", "tqs_batch_create", "tqs_batch_execute", "tqs_batch_counts",
@@ -129,6 +130,8 @@ def lib():
             L.tqs_plan_execute.restype = st
             L.tqs_plan_workspace_bytes.argtypes = [vp]
             L.tqs_plan_workspace_bytes.restype = C.c_size_t
+            L.tqs_plan_host_pool_bytes.argtypes = [vp]
+            L.tqs_plan_host_pool_bytes.restype = C.c_size_t
             L.tqs_plan_destroy.argtypes = [vp]
             L.tqs_debug_node_state.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.POINTER(tqs_options),
                                                C.c_uint32, C.c_uint64, dp]
@@ -318,6 +321,10 @@ def tqs_plan_execute(plan: Handle, seed: int, d_counts: int, report: bool = Fals
 
 def tqs_plan_workspace_bytes(plan: Handle) -> int:
     return int(lib().tqs_plan_workspace_bytes(plan.ptr))
+
+
+def tqs_plan_host_pool_bytes(plan: Handle) -> int:
+    return int(lib().tqs_plan_host_pool_bytes(plan.ptr))
 
 
 def tqs_plan_destroy(plan: Handle) -> None:

@@ -274,6 +274,8 @@ tqs_status tqs_plan_create(const tqs_circuit *c, const tqs_noise *nz, uint64_t s
 
 size_t tqs_plan_workspace_bytes(const tqs_plan *p) { return p ? p->dp.ws_bytes : 0; }
 
+size_t tqs_plan_host_pool_bytes(const tqs_plan *p) { return p ? p->dp.host_pool_bytes : 0; }
+
 void tqs_plan_destroy(tqs_plan *p) { delete p; }
 
 tqs_status tqs_plan_execute(tqs_plan *p, uint64_t seed, uint64_t *d_counts, tqs_report *report)
@@ -369,10 +371,10 @@ tqs_status tqs_debug_node_state(const tqs_circuit *c, const tqs_noise *nz, uint6
     std::vector<float> raw32;
     cudaError_t e;
     if (f64) {
-        e = cudaMemcpyAsync(raw.data(), p->dp.state[level], 16 * dim, cudaMemcpyDeviceToHost, p->dp.stream);
+        e = cudaMemcpyAsync(raw.data(), p->dp.state[level], 16 * dim, cudaMemcpyDefault, p->dp.stream);
     } else {
         raw32.resize(2 * dim);
-        e = cudaMemcpyAsync(raw32.data(), p->dp.state[level], 8 * dim, cudaMemcpyDeviceToHost, p->dp.stream);
+        e = cudaMemcpyAsync(raw32.data(), p->dp.state[level], 8 * dim, cudaMemcpyDefault, p->dp.stream);
     }
     const tqs::Level &lv = H.levels[level];
     const uint32_t np = lv.pass_end - lv.pass_begin;

@@ -3,6 +3,7 @@
 // sibling-consecutive node instances per level (Sec. 3.1), so the live state
 // pool is one chunk per level.
 #include <cuda_runtime.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <cmath>
@@ -76,12 +77,38 @@ void DevicePlan::release()
         cudaFree(ws);
     ws = nullptr;
     own_ws = false;
+    if (host_pool)
+        cudaFreeHost(host_pool);
+    host_pool = host_pool_dev = nullptr;
+    host_pool_bytes = 0;
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     ev0 = ev1 = nullptr;
 }
 
-// Workspace layout for `B` slots per level.
+// Whether level i keeps node states: every level but the leaves, whose last
+// pass only measures (unless the leaves need several passes or are kept).
+bool DevicePlan::level_needs_state(uint32_t i) const
+{
+    const PlanHost &H = host;
+    const Level &lv = H.levels[i];
+    const bool leaf = i + 1 == (uint32_t)H.levels.size();
+    return !leaf || lv.pass_end - lv.pass_begin > 1 || store_leaves;
+}
+
+size_t DevicePlan::host_state_bytes(uint64_t B) const
+{
+    const PlanHost &H = host;
+    const size_t sbytes = ((size_t)1 << H.n) * (H.prec == TQS_FP64 ? 16 : 8);
+    size_t total = 0;
+    for (uint32_t i = 0; i < (uint32_t)H.levels.size(); i++)
+        if (((host_mask >> i) & 1u) && level_needs_state(i))
+            total += align256(sbytes * B);
+    return total;
+}
+
+// Workspace layout for `B` slots per level (the levels in host_mask keep their
+// state slots in the host pool instead).
 size_t DevicePlan::layout(uint64_t B, bool assign)
 {
     const PlanHost &H = host;
@@ -104,13 +131,20 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
     size_t o_fid = take(sizeof(double) * (3 + 3 * 256));
     size_t o_perm = take(32);
     size_t o_counts = take(sizeof(uint64_t) * ((size_t)1 << H.n));
-    std::vector<size_t> o_state(L), o_noise(L), o_meta(L);
+    std::vector<size_t> o_state(L), o_noise(L), o_meta(L), h_state(L, 0);
+    size_t hoff = 0;
     for (uint32_t i = 0; i < L; i++) {
         const Level &lv = H.levels[i];
         const uint32_t np = lv.pass_end - lv.pass_begin;
-        const bool leaf = i + 1 == L;
-        const bool needs_state = !leaf || np > 1 || store_leaves;
-        o_state[i] = needs_state ? take(sbytes * B) : (size_t)-1;
+        if (!level_needs_state(i)) {
+            o_state[i] = (size_t)-1;
+        } else if ((host_mask >> i) & 1u) {
+            o_state[i] = (size_t)-2;
+            h_state[i] = hoff;
+            hoff = align256(hoff + sbytes * B);
+        } else {
+            o_state[i] = take(sbytes * B);
+        }
         o_noise[i] = take(std::max<size_t>(lv.g1 - lv.g0, 1) * B);
         o_meta[i] = take(sizeof(NodeMeta) * (np + 1) * B);
     }
@@ -132,7 +166,12 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
         noise.assign(L, nullptr);
         meta.assign(L, nullptr);
         for (uint32_t i = 0; i < L; i++) {
-            state[i] = o_state[i] == (size_t)-1 ? nullptr : (void *)(b + o_state[i]);
+            if (o_state[i] == (size_t)-1)
+                state[i] = nullptr;
+            else if (o_state[i] == (size_t)-2)
+                state[i] = (void *)((char *)host_pool_dev + h_state[i]);
+            else
+                state[i] = (void *)(b + o_state[i]);
             noise[i] = (uint8_t *)(b + o_noise[i]);
             meta[i] = (NodeMeta *)(b + o_meta[i]);
         }
@@ -156,6 +195,14 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
     uint64_t want = o.batch ? o.batch : std::max<uint64_t>(64, 65536 / tiles);
     want = std::min<uint64_t>(want, 65535);
     want = std::min<uint64_t>(want, maxact);
+    const uint32_t L = (uint32_t)H.levels.size();
+    host_mask = 0;
+    if (o.flags & TQS_FLAG_HOST_POOL) {
+        for (uint32_t i = 0; i < L; i++)
+            if (level_needs_state(i))
+                host_mask |= 1u << i;
+        per_slot = layout(1, false) - fixed + 256 * 8;
+    }
     size_t budget;
     if (o.workspace) {
         budget = o.workspace_bytes > fixed ? o.workspace_bytes - fixed : 0;
@@ -167,10 +214,37 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
             budget = o.workspace_bytes;  // a cap on what the library allocates
         budget = budget > fixed ? budget - fixed : 0;
     }
+    if (!o.workspace && !(o.flags & TQS_FLAG_HOST_POOL)) {
+        // one node per level does not fit in device memory: move the state slots
+        // of the upper levels (the fewest node instances) to the host pool until
+        // it does
+        for (uint32_t i = 0; i < L && per_slot > budget; i++) {
+            if (!level_needs_state(i))
+                continue;
+            host_mask |= 1u << i;
+            per_slot = layout(1, false) - fixed + 256 * 8;
+        }
+    }
     uint64_t B = std::min<uint64_t>(want, budget / std::max<size_t>(per_slot, 1));
     if (B == 0) {
         err = "workspace too small for one node per level (" + std::to_string(fixed + per_slot) + " bytes needed)";
         return TQS_ENOMEM;
+    }
+    if (host_mask) {
+        // the host pool takes at most a quarter of the host's physical memory
+        const long pages = sysconf(_SC_PHYS_PAGES), psz = sysconf(_SC_PAGE_SIZE);
+        const size_t cap = (pages > 0 && psz > 0) ? (size_t)pages * (size_t)psz / 4 : ((size_t)16 << 30);
+        const size_t per_host = std::max<size_t>(host_state_bytes(1), 1);
+        B = std::min<uint64_t>(B, std::max<uint64_t>(1, cap / per_host));
+        host_pool_bytes = host_state_bytes(B);
+        if (cudaHostAlloc(&host_pool, host_pool_bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            host_pool = nullptr;
+            err = "pinned host allocation of " + std::to_string(host_pool_bytes) + " bytes for the state pool failed";
+            host_pool_bytes = 0;
+            return TQS_ENOMEM;
+        }
+        CK(cudaHostGetDevicePointer(&host_pool_dev, host_pool, 0));
     }
     batch = B;
     ws_bytes = layout(B, false);

@@ -34,6 +34,16 @@ struct DevicePlan {
     uint8_t *d_perm = nullptr;
     unsigned long long *d_counts_internal = nullptr;
     double *d_S = nullptr;
+    // Levels whose state slots live in pinned host memory mapped into the
+    // device's address space (bit i = level i): the pass kernels read and write
+    // them in place (on a Grace-Blackwell node over NVLink-C2C), so the state pool
+    // is no longer bounded by HBM (Sec. 3.3-3.4: idle host memory holds
+    // intermediate states).  Set by create() under TQS_FLAG_HOST_POOL, or when
+    // the library allocates the workspace and one node per level does not fit.
+    uint32_t host_mask = 0;
+    void *host_pool = nullptr;      // cudaHostAlloc'd, mapped
+    void *host_pool_dev = nullptr;  // its device address
+    size_t host_pool_bytes = 0;
     std::vector<void *> state;
     std::vector<uint8_t *> noise;
     std::vector<NodeMeta *> meta;
@@ -53,6 +63,8 @@ struct DevicePlan {
     ~DevicePlan();
     void release();
     size_t layout(uint64_t B, bool assign);
+    bool level_needs_state(uint32_t i) const;
+    size_t host_state_bytes(uint64_t B) const;  // host pool for B slots per level
     tqs_status create(const tqs_options &o, std::string &err);
     tqs_status execute(uint64_t seed, unsigned long long *counts, bool timed, std::string &err);
     tqs_status run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vector<uint64_t> &plo,

@@ -11,6 +11,9 @@ headline one (which bench.py measures): one JSON line per configuration.
   qft26 / rc26   26-qubit QFT (32,768 shots) and random 26x30 circuit (2,048
                  shots: its ~30 passes per level make 32,768 shots a minutes-long
                  run), 512 MiB FP32 states, tree FP32 (DCP)
+  qft20_host     the 20-qubit QFT, 32,000 shots, tree FP32, with the state pool
+                 in device memory and in mapped host memory (not in the default
+                 list)
 
 Device time comes from the library's CUDA events (report.kernel_ms); noise
 p1 = 1e-3, p2 = 1e-2, pm = 2e-2 throughout.  Inputs are synthetic circuits of
@@ -82,6 +85,27 @@ def batch64(reps, autotune):
             "shots_per_s": total / (best * 1e-3), "graph_replay": True, "create_s": create_s}
 
 
+def host_pool(name, circ, shots, reps):
+    """Tree FP32 with the state pool in device memory and in mapped host memory
+    (TQS_FLAG_HOST_POOL: the pass kernels read parents from and write children
+    to host memory in place)."""
+    c, nz = capi.circuit(circ), capi.tqs_noise_model(*NOISE)
+    d = _device_counts(circ.n)
+    out = {"config": name, "n": circ.n, "gates": len(circ.gates), "shots": shots}
+    for label, flags in (("device_pool", 0), ("host_pool", capi.TQS_FLAG_HOST_POOL)):
+        t0 = time.perf_counter()
+        plan = capi.tqs_plan_create(c, nz, shots, capi.options(prec="fp32", flags=flags))
+        create_s = time.perf_counter() - t0
+        capi.tqs_plan_execute(plan, 0, d.data_ptr())
+        ms = [capi.tqs_plan_execute(plan, 1 + r, d.data_ptr(), report=True)["kernel_ms"] for r in range(reps)]
+        out[label] = {"ms": min(ms), "shots_per_s": shots / (min(ms) * 1e-3), "create_s": create_s,
+                      "host_pool_bytes": capi.tqs_plan_host_pool_bytes(plan),
+                      "workspace_bytes": capi.tqs_plan_workspace_bytes(plan)}
+        plan.close()
+    out["host_over_device"] = out["host_pool"]["shots_per_s"] / out["device_pool"]["shots_per_s"]
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--config", nargs="*", default=["qft16", "rc16", "batch64", "qft26", "rc26"])
@@ -97,6 +121,8 @@ def main(argv=None):
             r = single(name, qft(26), 32768, 1, modes=(("tree", "fp32"),))
         elif name == "rc26":
             r = single(name, random_layers(26, 30, 26030), 2048, 1, modes=(("tree", "fp32"),))
+        elif name == "qft20_host":
+            r = host_pool(name, qft(20), 32000, a.reps)
         elif name == "batch64":
             r = batch64(a.reps, a.autotune)
         else:
