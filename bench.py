@@ -64,10 +64,15 @@ def load_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the files the pass kernel is compiled and launched from: its six
+    instantiation units, the headers of csrc they include, and kernels.cu (which
+    sets its grid and shared memory).  Host-only sources do not enter."""
+    d = os.path.join(ROOT, "paper_2203_13892_gb300", "csrc")
+    names = sorted(f for f in os.listdir(d) if f.startswith("pass_") and f.endswith(".cu"))
+    names += ["pass_kernel.cuh", "pass_kernel.h", "device_common.cuh", "internal.h", "kernels.cu"]
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2203_13892_gb300", "csrc"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(ROOT, "paper_2203_13892_gb300", "csrc", f), "rb").read())
+    for f in names:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -177,7 +177,8 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
 uint64_t threshold32(double p);
 
 // ---------------------------------------------------------------------------
-// Kernel launchers (kernels.cu; the pass kernel itself is in pass_kernel.cuh).  All return the cudaError_t of the launch as int.
+// Kernel launchers (kernels.cu; the pass kernel itself is in pass_kernel.cuh).
+// All return the cudaError_t of the launch as int.
 // ---------------------------------------------------------------------------
 struct DevTables {
     const Instr *instr;
