@@ -319,6 +319,14 @@ tqs_status tqs_simulate(const tqs_circuit *c, const tqs_noise *nz, uint64_t shot
     st = p->dp.check_device_error(err);
     if (st != TQS_OK)
         return fail(st, err);
+    // the fidelity (from the device histogram) before any output is written,
+    // so that a failure there leaves the caller's buffers untouched
+    double F = std::numeric_limits<double>::quiet_NaN(), Fs = F;
+    if (!(o.flags & TQS_FLAG_NO_FIDELITY)) {
+        st = fidelity(c, shots, p->dp.d_counts_internal, s, &F, &Fs);
+        if (st != TQS_OK)
+            return st;
+    }
     const size_t bytes = sizeof(uint64_t) * ((size_t)1 << c->c.n);
     cudaError_t e = cudaMemcpyAsync(counts, p->dp.d_counts_internal, bytes, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
@@ -327,12 +335,6 @@ tqs_status tqs_simulate(const tqs_circuit *c, const tqs_noise *nz, uint64_t shot
         return fail(TQS_ECUDA, tqs::cuda_msg("simulate", (int)e));
     float ms = 0;
     cudaEventElapsedTime(&ms, p->dp.ev0, p->dp.ev1);
-    double F = std::numeric_limits<double>::quiet_NaN(), Fs = F;
-    if (!(o.flags & TQS_FLAG_NO_FIDELITY)) {
-        st = fidelity(c, shots, p->dp.d_counts_internal, s, &F, &Fs);
-        if (st != TQS_OK)
-            return st;
-    }
     if (fid)
         *fid = F;
     if (report) {
