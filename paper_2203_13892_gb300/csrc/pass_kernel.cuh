@@ -17,6 +17,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "device_common.cuh"
 #include "pass_kernel.h"
 
@@ -1182,10 +1184,15 @@ template <typename R, int MODE, int LOGR, bool FUSE> static int set_pass_attr()
 template <typename R, int MODE, int LOGR, bool FUSE>
 static int launch_pass_t(const PassK &k, dim3 grid, size_t smem, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
+    // the dynamic shared-memory limit is an attribute of the function on each
+    // device: raise it once per device that launches this instantiation
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done.load(std::memory_order_acquire) & bit)) {
         set_pass_attr<R, MODE, LOGR, FUSE>();
-        attr = true;
+        done.fetch_or(bit, std::memory_order_acq_rel);
     }
     pass_kernel<R, MODE, LOGR, FUSE><<<grid, kThreads, smem, st>>>(k);
     return (int)cudaGetLastError();
