@@ -17,8 +17,8 @@
  *
  * Parity status: the state-vector, noise, sampling and tree routines are pinned
  * by closed forms, invariants and the density-matrix oracle in the test suite.
- * The Philox stream is pinned by the generator's published known-answer
- * vectors and, beyond them, by statistical tests.
+ * The Philox stream is pinned statistically only (no published known-answer
+ * vectors are available here).
  */
 #include <complex.h>
 #include <math.h>
