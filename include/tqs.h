@@ -53,7 +53,7 @@ typedef enum {
     TQS_ENOMEM = 2,       /* host or device allocation failed / workspace too small */
     TQS_ECUDA = 3,        /* a CUDA call failed (message in tqs_last_error) */
     TQS_ETIMEOUT = 4,     /* a bounded device wait gave up */
-    TQS_EUNSUPPORTED = 5  /* valid request outside what this build supports */
+    TQS_EUNSUPPORTED = 5  /* valid request outside what this library supports */
 } tqs_status;
 
 typedef enum {
