@@ -10,8 +10,9 @@ printed value in the tests):
   * z = 1.96, eps = 0.05 (the paper gives neither); they reproduce (250,2,2)
     for QPE_9 at 1000 shots (Sec. 5.6) and A_0 = 500 with seven subcircuits
     for QFT_14 at 32,000 shots (Sec. 5.1).
-  * "incrementing shots from the first subcircuit onward" is read as
-    A_0 = ceil(N / A_r^k), which makes the leaf count reach N.
+  * the top-up of the uniform arities until the leaves reach the requested
+    shot count (Sec. 3.2.4 adds shots one at a time from the first subcircuit
+    on) is read as A_0 = ceil(N / A_r^k).
   * all k+1 subcircuits get an equal share of the gates (this matches the
     printed 3.53x theoretical speedup of QFT_14, Sec. 5.1).
   * the copy-cost limit bounds the subcircuit count: every subcircuit needs at
