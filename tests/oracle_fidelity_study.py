@@ -1,8 +1,8 @@
 """Tree mode against plain baseline mode in normalised fidelity (Sec. 4.1, the
 comparison of Sec. 5.4), computed with the FP64 oracle on the 16-qubit
 configurations: 8,192 shots, p1 = 1e-3, p2 = 1e-2, pm = 2e-2, the DCP tree, seeds
-0..S-1.  The GPU path's FP64 histograms are bit-exact with the oracle's for these
-configurations (tests/test_gpu_configs.py), so the numbers are also the GPU's.
+0..S-1.  The GPU path's FP64 histograms are bit-exact with the oracle's wherever
+the GPU tests compare them (QFT-16 and RC-16x40 at these sizes among them).
 
 For each seed: F of the tree histogram and of the baseline histogram against the
 noiseless distribution, their difference, and for scale the difference between
