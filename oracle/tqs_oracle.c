@@ -17,8 +17,9 @@
  *
  * Parity status: the state-vector, noise, sampling and tree routines are pinned
  * by closed forms, invariants and the density-matrix oracle in the test suite.
- * The Philox stream is pinned statistically only (no published known-answer
- * vectors are available here).
+ * The Philox stream is pinned word for word against PyTorch's ATen
+ * Philox4x32-10 engine, an independent implementation, on 12,000 counter/key
+ * pairs, and statistically (uniformity, avalanche).
  */
 #include <complex.h>
 #include <math.h>

@@ -1,11 +1,15 @@
 """Pins of the oracle's random draws and noise channels.
 
-The Philox stream itself is pinned statistically (uniformity, avalanche,
-independence of the counter domains); no published known-answer vectors are
-available here.  The channels are pinned by closed forms of the depolarizing
-and readout channels (Sec. 4.3) on states where the outcome distribution is
-known exactly."""
+The Philox stream is pinned word for word against an independent
+implementation, PyTorch's ATen Philox4x32-10 engine (compiled here from its
+header by `philox_ref_aten.cpp`), and statistically (uniformity, avalanche,
+independence of the counter domains).  The channels are pinned by closed forms
+of the depolarizing and readout channels (Sec. 4.3) on states where the outcome
+distribution is known exactly."""
 import math
+import os
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -19,6 +23,57 @@ def _words(orc, count, seed=12345, domain=7):
     for i in range(count):
         out[i] = orc.core.philox([i & 0xFFFFFFFF, i >> 32, 3, domain], [seed & 0xFFFFFFFF, seed >> 32])
     return out
+
+
+def _aten_philox(tmp_path, rows):
+    """Philox4x32-10 outputs of PyTorch's ATen engine for rows of (c0..c3, k0, k1)."""
+    import torch.utils.cpp_extension as ext
+
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ is needed to compile the ATen Philox reference")
+    exe = str(tmp_path / "philox_ref_aten")
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "philox_ref_aten.cpp")
+    inc = []
+    for d in ext.include_paths():
+        inc += ["-I", d]
+    subprocess.run([gxx, "-std=c++17", "-O1", *inc, src, "-o", exe], check=True, capture_output=True)
+    text = "\n".join(" ".join(str(int(x)) for x in r) for r in rows) + "\n"
+    out = subprocess.run([exe], input=text, capture_output=True, text=True, check=True).stdout.split()
+    return np.array(out, dtype=np.uint64).reshape(-1, 4)
+
+
+def test_philox_matches_aten_engine(orc, tmp_path):
+    """Every output word of the oracle's Philox4x32-10 equals that of PyTorch's
+    ATen engine, an implementation written independently of this one, on
+    12,000 (counter, key) pairs: the all-zero and all-ones inputs, single set
+    bits in every counter and key word, counter words next to their carry
+    boundaries, the counter layouts of the noise, measurement and readout
+    draws, and uniformly random inputs."""
+    M = 0xFFFFFFFF
+    rows = [[0] * 6, [M] * 6, [0, 0, 0, 0, M, M], [M, M, M, M, 0, 0]]
+    for w in range(6):
+        for b in range(32):
+            r = [0] * 6
+            r[w] = 1 << b
+            rows.append(r)
+            r2 = [M] * 6
+            r2[w] ^= 1 << b
+            rows.append(r2)
+    for v in (M - 1, M, 0x7FFFFFFF, 0x80000000):
+        rows.append([v, v, v, v, 7, 9])
+    rng = np.random.default_rng(2203)
+    for dom in (1, 2, 3):  # (node_lo, node_hi, site, domain) with 64-bit seeds
+        for _ in range(500):
+            node = int(rng.integers(0, 2**40))
+            seed = int(rng.integers(0, 2**63))
+            rows.append([node & M, node >> 32, int(rng.integers(0, 1200)), dom, seed & M, seed >> 32])
+    while len(rows) < 12000:
+        rows.append([int(x) for x in rng.integers(0, 2**32, 6, dtype=np.uint64)])
+    want = _aten_philox(tmp_path, rows)
+    got = np.array([orc.core.philox(r[:4], r[4:]) for r in rows], dtype=np.uint64)
+    bad = np.nonzero((got != want).any(axis=1))[0]
+    assert bad.size == 0, ("first mismatch", rows[bad[0]], got[bad[0]], want[bad[0]])
 
 
 def test_philox_uniform_bytes(orc):
