@@ -53,7 +53,9 @@ typedef enum {
     TQS_ENOMEM = 2,       /* host or device allocation failed / workspace too small */
     TQS_ECUDA = 3,        /* a CUDA call failed (message in tqs_last_error) */
     TQS_ETIMEOUT = 4,     /* a bounded device wait gave up */
-    TQS_EUNSUPPORTED = 5  /* valid request outside what this library supports */
+    TQS_EUNSUPPORTED = 5, /* valid request outside what this library supports */
+    TQS_EBOUNDS = 6       /* a device-side index check (TQS_FLAG_DEBUG_BOUNDS) found an index out of
+                             range; the offending access was skipped and the results are invalid */
 } tqs_status;
 
 typedef enum {
@@ -116,6 +118,21 @@ typedef enum {
                                      per level moves the upper levels' slots there by itself.  At most a
                                      quarter of the host's physical memory is pinned (the node batch
                                      shrinks to fit); ignored by tqs_simulate_static. */
+
+#define TQS_FLAG_DEBUG_BOUNDS 0x20u /* every state-pass CTA checks, before its first memory access, that its
+                                       output slot, input slot and every tile and outside-tile bit lie inside
+                                       the buffers and the state; a CTA that fails writes the device error
+                                       word, touches no memory and returns, and the call returns
+                                       TQS_EBOUNDS (no trap).  Off by default: the check costs a few
+                                       instructions per CTA. */
+#define TQS_FLAG_FAULT_TIMEOUT 0x40u /* test only: fused tensor-core blocks (TQS_FLAG_FUSE) issue no MMA
+                                        and no commit and wait with a short iteration cap, so their
+                                        bounded wait gives up with no work in flight; the call returns
+                                        TQS_ETIMEOUT and the library stays usable */
+#define TQS_FLAG_FAULT_BOUNDS 0x80u  /* test only, with TQS_FLAG_DEBUG_BOUNDS: the executor tells the
+                                        kernels that the output pool holds one slot fewer than it does,
+                                        so the last node of a full launch fails the check above (no
+                                        access is made out of range) */
 
 /* Kernel classes timed under TQS_FLAG_PROFILE (index into report.prof_*). */
 #define TQS_PROF_NOISE 0   /* Philox noise draws + Pauli frames */
@@ -305,10 +322,15 @@ tqs_status tqs_debug_plan_order(const tqs_circuit *c, const tqs_noise *nz, uint6
  *
  * d_counts: caller-owned DEVICE array of 2^n uint64, zeroed by the call, then
  * the histogram (sums to shots).  The call runs on opts->stream and returns
- * after the simulation has finished.  The first call on each device (with that
- * device current) looks up the array's device address once; make that first
- * call before any stream capture.  Every call shares the one array: calls whose
- * GPU work overlaps (different streams or threads) race on it, so serialise them. */
+ * after the simulation has finished; it uploads the plan's tables and
+ * synchronises that stream, so it must not be called on a stream that is being
+ * captured.  The first call on each device (with that device current) looks up
+ * the array's device address and keeps it for the rest of the process; do not
+ * call this again on a device after cudaDeviceReset() of that device.  Every
+ * call shares the one array and it keeps the last call's contents: calls whose
+ * GPU work overlaps (different streams or threads) race on it, so serialise
+ * them.  opts->part = TQS_PART_LEARNED returns TQS_EUNSUPPORTED (the network
+ * behind it allocates device memory). */
 #define TQS_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
 tqs_status tqs_simulate_static(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, uint64_t seed,
                                const tqs_options *opts, uint64_t *d_counts);

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-TQS_OK, TQS_EINVAL, TQS_ENOMEM, TQS_ECUDA, TQS_ETIMEOUT, TQS_EUNSUPPORTED = range(6)
+TQS_OK, TQS_EINVAL, TQS_ENOMEM, TQS_ECUDA, TQS_ETIMEOUT, TQS_EUNSUPPORTED, TQS_EBOUNDS = range(7)
 TQS_MODE_BASELINE, TQS_MODE_TREE = 0, 1
 TQS_FP64, TQS_FP32 = 0, 1
 TQS_PART_DCP, TQS_PART_UCP, TQS_PART_XCP, TQS_PART_EXPLICIT, TQS_PART_LEARNED = range(5)
@@ -25,6 +25,9 @@ TQS_FLAG_PROFILE = 0x2
 TQS_FLAG_AUTOTUNE = 0x4
 TQS_FLAG_FUSE = 0x8
 TQS_FLAG_HOST_POOL = 0x10
+TQS_FLAG_DEBUG_BOUNDS = 0x20
+TQS_FLAG_FAULT_TIMEOUT = 0x40
+TQS_FLAG_FAULT_BOUNDS = 0x80
 TQS_MAX_LEVELS = 17
 TQS_PROF_KINDS = 4
 PROF_NAMES = ("noise", "store", "sums", "sample")

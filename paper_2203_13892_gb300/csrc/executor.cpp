@@ -128,9 +128,9 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
     size_t o_fused = take(sizeof(float) * std::max<size_t>(H.fused.size(), 4));
     size_t o_err = take(sizeof(unsigned int) * 4);
     size_t o_choff = take(sizeof(uint32_t) * std::max<size_t>(H.chunk_off.size(), 1));
-    size_t o_fid = take(sizeof(double) * (3 + 3 * 256));
+    size_t o_fid = take(caller_counts ? 0 : sizeof(double) * (3 + 3 * 256));
     size_t o_perm = take(32);
-    size_t o_counts = take(sizeof(uint64_t) * ((size_t)1 << H.n));
+    size_t o_counts = take(caller_counts ? 0 : sizeof(uint64_t) * ((size_t)1 << H.n));
     std::vector<size_t> o_state(L), o_noise(L), o_meta(L), h_state(L, 0);
     size_t hoff = 0;
     for (uint32_t i = 0; i < L; i++) {
@@ -159,9 +159,9 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
         d_fused = (float *)(b + o_fused);
         d_err = (unsigned int *)(b + o_err);
         d_chunk_off = (uint32_t *)(b + o_choff);
-        d_fid = (double *)(b + o_fid);
+        d_fid = caller_counts ? nullptr : (double *)(b + o_fid);
         d_perm = (uint8_t *)(b + o_perm);
-        d_counts_internal = (unsigned long long *)(b + o_counts);
+        d_counts_internal = caller_counts ? nullptr : (unsigned long long *)(b + o_counts);
         state.assign(L, nullptr);
         noise.assign(L, nullptr);
         meta.assign(L, nullptr);
@@ -295,6 +295,21 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
     return TQS_OK;
 }
 
+// Index checks and fault injection of the options (TQS_FLAG_DEBUG_BOUNDS,
+// TQS_FLAG_FAULT_TIMEOUT, TQS_FLAG_FAULT_BOUNDS) for one pass launch.
+void DevicePlan::set_debug(PassLaunch &a) const
+{
+    a.dbg = 0;
+    if (opts.flags & TQS_FLAG_DEBUG_BOUNDS)
+        a.dbg |= kDbgBounds;
+    if (opts.flags & TQS_FLAG_FAULT_TIMEOUT)
+        a.dbg |= kDbgFaultTimeout;
+    a.in_slots = batch;
+    a.out_slots = batch;
+    if ((opts.flags & TQS_FLAG_FAULT_BOUNDS) && batch > 0)
+        a.out_slots = batch - 1;  // understated on purpose: the kernels' own check must catch it
+}
+
 tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vector<uint64_t> &plo,
                                  uint64_t seed, unsigned long long *counts, std::string &err)
 {
@@ -349,6 +364,7 @@ tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vect
         a.fused = ps.fused_blocks ? d_fused : nullptr;
         a.fused_k = ps.fused_blocks ? H.fused_k : 0;
         a.err = d_err;
+        set_debug(a);
         a.n = H.n;
         a.t = ps.t;
         a.L = ps.L;
@@ -479,6 +495,7 @@ tqs_status DevicePlan::run_chain(uint32_t level, uint64_t node, uint64_t seed, s
             a.fused = ps.fused_blocks ? d_fused : nullptr;
             a.fused_k = ps.fused_blocks ? H.fused_k : 0;
             a.err = d_err;
+            set_debug(a);
             a.n = H.n;
             a.t = ps.t;
             a.L = ps.L;
@@ -499,16 +516,24 @@ tqs_status DevicePlan::run_chain(uint32_t level, uint64_t node, uint64_t seed, s
 
 tqs_status DevicePlan::check_device_error(std::string &err)
 {
-    unsigned int h = 0;
-    CK(cudaMemcpyAsync(&h, d_err, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    unsigned int h[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(h, d_err, sizeof(h), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
-    if (h) {
-        CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned int), stream));
-        if (h & 2u) {
+    if (h[0]) {
+        CK(cudaMemsetAsync(d_err, 0, 4 * sizeof(unsigned int), stream));
+        CK(cudaStreamSynchronize(stream));
+        if (h[0] & 2u) {
             err = "internal: a fused-gate record reached a kernel built without the tensor-core path";
             return TQS_ECUDA;
         }
-        err = "a bounded tensor-core wait gave up (device error word " + std::to_string(h) + ")";
+        if (h[0] & 4u) {
+            static const char *what[] = {"?", "output slot", "input slot", "tile width", "tile bit",
+                                         "outside-tile bit"};
+            err = std::string("device index check failed: ") + what[h[1] < 6 ? h[1] : 0] + " " +
+                  std::to_string(h[2]) + " out of range; the access was skipped";
+            return TQS_EBOUNDS;
+        }
+        err = "a bounded tensor-core wait gave up (device error word " + std::to_string(h[0]) + ")";
         return TQS_ETIMEOUT;
     }
     return TQS_OK;

@@ -17,6 +17,7 @@ struct DevicePlan {
     tqs_options opts{};
     cudaStream_t stream = nullptr;
     bool store_leaves = false;  // keep leaf states (debug chains)
+    bool caller_counts = false; // the layout reserves no internal histogram and no fidelity scratch
     const uint64_t *seed_dev = nullptr;  // device seed read by the kernels (graph replays)
     uint64_t batch = 0;         // node instances per chunk and level
     void *ws = nullptr;
@@ -72,6 +73,7 @@ struct DevicePlan {
     tqs_status run_chain(uint32_t level, uint64_t node, uint64_t seed, std::string &err);
     // reads and clears the device error word (synchronises the stream)
     tqs_status check_device_error(std::string &err);
+    void set_debug(PassLaunch &a) const;
     bool profiling() const { return (opts.flags & TQS_FLAG_PROFILE) != 0; }
 };
 

@@ -235,8 +235,13 @@ struct PassLaunch {
     uint64_t seed, thrm;
     const float *fused;        // fused-gate operands (device), nullptr when the pass has none
     uint32_t fused_k;          // qubits per fused gate (0: none)
-    unsigned int *err;         // device error word: bit 0 = a bounded tensor-core wait gave up
+    unsigned int *err;         // device error words: [0] bits (1 = a bounded tensor-core wait gave up,
+                               // 2 = a fused record reached a kernel without the tensor-core path,
+                               // 4 = an index check failed), [1] check code, [2] offending value
+    uint32_t dbg;              // kDbgBounds | kDbgFaultTimeout
+    uint64_t in_slots, out_slots;  // state slots of the input and output buffers (index checks)
 };
+constexpr uint32_t kDbgBounds = 1u, kDbgFaultTimeout = 2u;
 int launch_pass(const PassLaunch &a, void *stream);
 // Sets the shared-memory limits of every kernel variant (call before a stream capture).
 int prepare_kernels();

@@ -126,6 +126,9 @@ int launch_pass(const PassLaunch &a, void *stream)
     k.fused = a.fused;
     k.fused_k = a.fused ? a.fused_k : 0;
     k.err = a.err;
+    k.dbg = a.dbg;
+    k.in_slots = a.in_slots;
+    k.out_slots = a.out_slots;
     k.thrm = a.thrm;
     k.ibeg = a.ibeg;
     k.iend = a.iend;

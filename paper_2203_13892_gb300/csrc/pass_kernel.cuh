@@ -463,6 +463,42 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
 
     const uint32_t slot = (MODE == MODE_SAMPLE) ? blockIdx.x : blockIdx.y;
     const uint64_t node = a.node_lo + slot;
+    if (a.dbg & kDbgBounds) {
+        // index check before the first memory access: every state index this CTA
+        // forms is (outside-tile bits | tile bits) of its slot's state, so checking
+        // the slots and the bit positions covers all of them
+        uint32_t code = 0;
+        uint64_t val = 0;
+        if ((uint64_t)slot >= a.out_slots) {
+            code = 1;
+            val = slot;
+        } else if (a.in && a.in_from_parent && node / a.arity - a.parent_lo >= a.in_slots) {
+            code = 2;
+            val = node / a.arity - a.parent_lo;
+        } else if (a.t > a.n || a.state_elems != (1ull << a.n)) {
+            code = 3;
+            val = a.t;
+        } else {
+            for (uint32_t j = 0; j < a.t && !code; j++)
+                if (a.tbits[j] >= a.n) {
+                    code = 4;
+                    val = a.tbits[j];
+                }
+            for (uint32_t b = 0; b < a.n - a.t && !code; b++)
+                if (a.hbits[b] >= a.n) {
+                    code = 5;
+                    val = a.hbits[b];
+                }
+        }
+        if (code) {
+            if (threadIdx.x == 0 && a.err) {
+                atomicOr(a.err, 4u);
+                if (atomicCAS(a.err + 1, 0u, code) == 0u)
+                    a.err[2] = (unsigned int)val;
+            }
+            return;  // uniform: nothing of this CTA touches memory
+        }
+    }
     const uint64_t seed = a.seed_dev ? *a.seed_dev : a.seed;
     const NodeMeta m0 = a.meta[(uint64_t)slot * a.meta_stride + a.pass_local];
     const NodeMeta m1 = a.meta[(uint64_t)slot * a.meta_stride + a.pass_local + 1];
@@ -504,6 +540,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     const uint32_t nzst_k = ((a.sites < (uint32_t)kNoiseStage ? a.sites : (uint32_t)kNoiseStage) + 15u) / 16u * 16u;
     unsigned char *fz = nullptr;
     uint32_t tc_cols = 0, tc_phase = 0;
+    bool tc_failed = false;  // CTA-uniform: a bounded tensor-core wait gave up; no more fused blocks
     if (FUSE && a.fused_k) {
         const size_t te_b = (size_t)(TE < (uint32_t)kThreads ? (uint32_t)kThreads : TE) * sizeof(C);
         size_t off = te_b + 256 * 2 + kThreads * 8 + 4 * 8 + 32 * 4 + nzst_k + kProgChunkBytes;
@@ -813,7 +850,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
             fence_async_smem();
             __syncthreads();
             tc_fence_after();
-            if (tid == 0) {
+            const bool fault = (a.dbg & kDbgFaultTimeout) != 0u;  // test: nothing is issued, the wait runs out
+            if (tid == 0 && !fault) {
                 const uint32_t idesc = tc_idesc_tf32(128, Kr);
                 const uint32_t sbo = Kr / 4 * 128;
                 const uint32_t sa[3] = {smem_u32(A_hi), smem_u32(A_hi), smem_u32(A_lo)};
@@ -824,18 +862,21 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                                     tc_smem_desc(sb[term] + ks * 256, 128, sbo), idesc, (term | ks) != 0);
                 tc_commit(mbar);
             }
-            const bool ok = mbar_wait_bounded(mbar, tc_phase, 1u << 22);
-            tc_phase ^= 1u;
+            const uint32_t cap = fault ? (1u << 10) : (1u << 22);
+            // one outcome for the whole CTA, so that every thread takes the same branch
+            const bool ok = __syncthreads_and(mbar_wait_bounded(mbar, tc_phase, cap) ? 1 : 0) != 0;
             tc_fence_after();
-            __syncthreads();
             if (!ok) {
                 if (tid == 0 && a.err)
                     atomicOr(a.err, 1u);
-                // give the products in flight a second bounded chance before TMEM is reused
-                mbar_wait_bounded(mbar, tc_phase ^ 1u, 1u << 22);
-                __syncthreads();
-                return;  // results of this block are not applied; the host reports TQS_ETIMEOUT
+                // products possibly still in flight get a second bounded wait before the
+                // TMEM they write is released at the end of the kernel
+                if (!fault)
+                    (void)__syncthreads_and(mbar_wait_bounded(mbar, tc_phase, cap) ? 1 : 0);
+                tc_failed = true;  // later fused blocks are skipped; the host reports TQS_ETIMEOUT
+                return;            // from fused_apply: v[] keeps the block's input, the tile region is stale
             }
+            tc_phase ^= 1u;
             // D[c][o] from TMEM: warp w reads rows 32*(w%4)..+31 (its lane quarter) and
             // one half of the Kr columns
             const uint32_t w = tid >> 5, lane = tid & 31u;
@@ -910,9 +951,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                     for (uint32_t x = hibeg + (tid & 31u); x < hiend; x += 32u)
                         anyf |= noise_at(a.instr[x].site);
                     const bool any = __any_sync(0xffffffffu, anyf != 0u);
-                    bool done = false;
+                    bool done = tc_failed;  // after a failed wait nothing more is computed
                     if constexpr (sizeof(R) == 4) {
-                        if (!any && a.fused_k == ha) {
+                        if (!done && !any && a.fused_k == ha) {
                             flush();
                             fused_apply(pay, ha);
                             done = true;

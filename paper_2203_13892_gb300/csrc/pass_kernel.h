@@ -26,6 +26,8 @@ struct PassK {
     const float *fused;
     unsigned int *err;
     uint64_t seed, thrm;
+    uint64_t in_slots, out_slots;
+    uint32_t dbg;
     uint32_t fused_k;
     uint32_t ibeg, iend, n, t, L, sites, meta_stride, pass_local;
     uint32_t chunk_begin, chunk_end;

@@ -6,10 +6,14 @@
 // library's module on every GPU that loads it; it stays reserved until the
 // process exits.  Host code cannot use the array's name as an address, so the
 // first call on each device (with that device current) resolves the address
-// with cudaGetSymbolAddress and caches it; make that first call before any
-// stream capture.  All calls on a device share the one array and it keeps the
-// last call's contents: calls whose work overlaps on the GPU (other streams,
-// other threads) race on it and must be serialised by the caller.
+// with cudaGetSymbolAddress and caches it for the rest of the process; the
+// cached address does not survive a cudaDeviceReset of that device.  The call
+// uploads tables and synchronises its stream, so it is never issued on a
+// stream that is being captured.  All calls on a device share the one array and
+// it keeps the last call's contents: calls whose work overlaps on the GPU
+// (other streams, other threads) race on it and must be serialised by the
+// caller.  The learned partitioner is refused here (TQS_EUNSUPPORTED): its
+// network runs through the library's allocating MLP kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -67,6 +71,10 @@ extern "C" tqs_status tqs_simulate_static(const tqs_circuit *c, const tqs_noise 
         tqs_options_default(&o);
     if (o.prec != TQS_FP32 && o.prec != TQS_FP64)
         return tqs::set_error(TQS_EINVAL, "unknown precision");
+    if (o.part == TQS_PART_LEARNED)
+        return tqs::set_error(TQS_EUNSUPPORTED,
+                              "the learned partitioner allocates device memory for its network; "
+                              "tqs_simulate_static takes DCP, UCP, XCP or an explicit tree");
     o.workspace = nullptr;  // the scratch is the static array
     o.workspace_bytes = 0;
     o.flags &= ~TQS_FLAG_PROFILE;  // no events are created on this path
@@ -86,6 +94,7 @@ extern "C" tqs_status tqs_simulate_static(const tqs_circuit *c, const tqs_noise 
     dp.opts = o;
     dp.stream = (cudaStream_t)o.stream;
     dp.store_leaves = false;
+    dp.caller_counts = true;  // the histogram is the caller's d_counts and no fidelity is computed
     const tqs::PlanHost &H = dp.host;
 
     // the largest batch whose workspace fits the static array

@@ -90,3 +90,37 @@ def test_config4_large_states(orc, name, shots):
     # and adds no rounding.  Bound: 8u per gate on the root-to-leaf path.
     tol = 8 * 2.0 ** -24 * len(circ.gates)
     assert abs(float(np.vdot(psi, psi).real) - 1.0) < tol
+
+
+@pytest.mark.parametrize("name,shots", [("qft26", 32768), ("rc26x30", 2048)])
+def test_config4_against_oracle(orc, name, shots):
+    """26-qubit states (512 MiB in FP32) against the FP64 oracle, whose chains at
+    this size take tens of seconds each: one node state element by element
+    (within 2e-5), and the oracle's outcomes of four sampled leaves present in
+    the device histogram at or next to their bin (FP32 rounding may move a
+    cumulative-probability boundary past a sample; with at most 32,768 shots
+    over 2^26 outcomes a wrong outcome lands on an occupied bin with
+    probability below 2e-3).  These tile passes gather more outside-tile bits
+    than any smaller configuration."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    circ = qft(26) if name == "qft26" else random_layers(26, 30, 26030)
+    c, nz = tqs.circuit(circ), tqs.tqs_noise_model(P1, P2, PM)
+    arity, split = tqs.tqs_partition(c, nz, shots, tqs.options())
+    L = len(arity)
+    leaves = [0, shots // 3, shots // 2 + 1, shots - 1]
+    level, node = (L - 1, shots // 2) if name == "qft26" else (0, 3)
+    with ThreadPoolExecutor(max_workers=len(leaves) + 1) as ex:
+        fut_state = ex.submit(orc.core.node_state, circ, P1, P2, 1, arity, split, level, node)
+        fut_leaves = [ex.submit(orc.core.leaf_outcome, circ, P1, P2, PM, 1, arity, split, m) for m in leaves]
+        counts, _, rep = tqs.tqs_simulate(c, nz, shots, 1, tqs.options(prec="fp32", flags=capi.TQS_FLAG_NO_FIDELITY),
+                                          n=circ.n)
+        got = tqs.tqs_debug_node_state(c, nz, shots, 1, tqs.options(prec="fp32"), level, node, circ.n)
+        want = fut_state.result()
+        ys = [f.result() for f in fut_leaves]
+    assert rep["arity"] == arity and int(counts.sum()) == shots
+    err = float(np.max(np.abs(got - want)))
+    assert err < 2e-5, (level, node, err)
+    for m, y in zip(leaves, ys):
+        near = counts[max(y - 1, 0):min(y + 2, 1 << circ.n)]
+        assert near.sum() > 0, (m, y)

@@ -60,3 +60,34 @@ def test_static_rejects_requests_beyond_the_array():
         tqs.tqs_simulate_static(c, nz, 100, 0, tqs.options(), d.data_ptr())
     assert e.value.status == capi.TQS_EINVAL
     assert "static scratch" in str(e.value)
+
+
+def test_static_uses_the_whole_array_for_states():
+    """QFT-20 in FP32 with three stored levels needs 24 MiB of states plus small
+    tables: it fits the 32 MiB array only because this path reserves no internal
+    histogram (8 MiB at 20 qubits) and no fidelity scratch."""
+    torch = pytest.importorskip("torch")
+    circ = qft(20)
+    G = len(circ.gates)
+    c, nz = tqs.circuit(circ), tqs.tqs_noise_model(1e-3, 1e-2, 2e-2)
+    o = tqs.options(prec="fp32", arity=[4, 2, 2, 2], split=[0, 55, 110, 165, G])
+    plan = tqs.tqs_plan_create(c, nz, 32, o)
+    ref = torch.zeros(1 << circ.n, dtype=torch.int64, device="cuda")
+    tqs.tqs_plan_execute(plan, 3, ref.data_ptr())
+    torch.cuda.synchronize()
+    for call in range(2):
+        d = _device_counts(torch, circ.n, 5)
+        tqs.tqs_simulate_static(c, nz, 32, 3, o, d.data_ptr())
+        assert np.array_equal(d.cpu().numpy(), ref.cpu().numpy()), call
+
+
+def test_static_refuses_the_learned_partitioner():
+    """The learned partitioner's network runs through allocating kernels, so the
+    allocation-free entry point refuses it before any device work."""
+    torch = pytest.importorskip("torch")
+    circ = qft(8)
+    c, nz = tqs.circuit(circ), tqs.tqs_noise_model(1e-3, 1e-2, 2e-2)
+    d = torch.zeros(1 << circ.n, dtype=torch.int64, device="cuda")
+    with pytest.raises(capi.TqsError) as e:
+        tqs.tqs_simulate_static(c, nz, 100, 0, tqs.options(part="learned"), d.data_ptr())
+    assert e.value.status == capi.TQS_EUNSUPPORTED
