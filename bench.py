@@ -352,8 +352,10 @@ def main():
             ba, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.fill_(1.0)
             ba.record(stream)
-            brep = tqs.tqs_plan_execute(bplan, 8 + r, bcounts.data_ptr(), report=(r == 0))
+            rep_r = tqs.tqs_plan_execute(bplan, 8 + r, bcounts.data_ptr(), report=(r == 0))
             bb.record(stream)
+        if r == 0:
+            brep = rep_r
         stream.synchronize()
         base_ms.append(ba.elapsed_time(bb) if r else None)
     # the first repeat carries the report (which synchronises): time the others
