@@ -40,8 +40,10 @@ static_assert(sizeof(Instr) == 16, "Instr layout");
 // where phi is the stored vector (physical bit order).
 struct NodeMeta {
     uint32_t mask;
-    uint32_t phase;
+    uint32_t phase;  // bits 0-1: i-power; bit 31 (entries 0..npass-1): the pass this entry opens
+                     // holds a Pauli of this node
 };
+constexpr uint32_t kMetaNoisy = 0x80000000u;
 
 // ---------------------------------------------------------------------------
 // Host-side circuit and plan
@@ -71,7 +73,11 @@ struct Noise {
 //               run of consecutive diagonal gates (and lazy SWAPs) it aggregates, then one
 //               GateEnt (+ 4 factors) per gate of the run
 // DENSE1 sets c = 1 when the matrix is real.  A factor record is an 8-byte FacHdr
-// followed by its complex value at the next multiple of sizeof(C) (16 or 32 bytes).
+// followed by its value at the next multiple of 8 (FP64: 32 bytes in all) or right
+// after it (FP32: 16 bytes).  Diagonal values (G, the factors, the gate entries'
+// four factors) are complex doubles in FP64 programs and phases in FP32 programs:
+// one uint32 per value, the angle in units of 2^-32 turns (every diagonal gate
+// kind has unit-modulus factors).
 // A run's factors: the product over its gates of D = G * prod a_q^{x_q} *
 // prod c_qr^{x_q x_r}, merged per qubit and per pair and classified by where
 // the bits live (thread bit, register slot bit, outside the tile).
@@ -81,7 +87,8 @@ struct Noise {
 //               the float offset of the operand in PlanHost::fused (u32) and three zero words.
 //               The kernels apply it as one 2^k x 2^k complex product on the tensor cores
 //               (FP32 states only, k = t - 7 so that a tile has 128 columns).
-enum RecType : uint8_t { REC_DENSE1 = 1, REC_DENSE2 = 2, REC_RUN = 3, REC_FUSED = 4 };
+//   REC_END     no payload: the end of the pass's program (every pass has one)
+enum RecType : uint8_t { REC_DENSE1 = 1, REC_DENSE2 = 2, REC_RUN = 3, REC_FUSED = 4, REC_END = 5 };
 enum FacKind : uint8_t {
     FAC_A_FIXED = 1,   // a^{x_p}, p a thread bit or outside the tile
     FAC_A_SLOT = 2,    // a^{x}, on slot bit s = j0 - 8
@@ -89,6 +96,26 @@ enum FacKind : uint8_t {
     FAC_C_MIXED = 5,   // c^{x_p0 x_s1}, p0 fixed, s1 = j1 - 8 a slot bit
     FAC_C_SLOTS = 7    // c^{x_s0 x_s1}, both slot bits
 };
+// FP32 programs: a REC_RUN record is RecHdr, then RunHdr32, then the factor
+// entries {mask, phase} (8 bytes each): nbase entries for the thread's base
+// phase, then ne[0] entries for slot 0's linear phase, ne[1] for slot 1, ...
+// An entry applies to a thread iff its logical bits (physical bits XOR the
+// frame mask) are 1 at every bit of `mask` (thread or outside-tile bits).
+// Factors on slot bits alone are the same for every thread and are summed on
+// the host into econst (linear, per slot) and gp (pairs, index hi(hi-1)/2+lo).
+// Then padding to 16 bytes and the GateEnt list (phases) as for FP64.
+constexpr uint32_t kMaxSlots = 5;
+struct RunHdr32 {
+    uint8_t nbase;
+    uint8_t ne[kMaxSlots];
+    uint16_t gused;            // pairs with a nonzero phase
+    uint8_t eused;             // slots with a nonzero econst
+    uint8_t pad[7];
+    uint32_t g0;               // global phase of the run
+    uint32_t econst[kMaxSlots];
+    uint32_t gp[kMaxSlots * (kMaxSlots - 1) / 2];
+};
+static_assert(sizeof(RunHdr32) == 80, "RunHdr32 layout");
 struct RecHdr {
     uint8_t type, a, b, c;
     uint8_t d, e;

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(256) noise_kernel(const __grid_constant__ Nois
     if (a.parent_meta) {
         const uint64_t ps = node / a.arity - a.parent_lo;
         par = a.parent_meta[ps * a.parent_stride + a.parent_end];
+        par.phase &= 3u;  // the parent's flags are not inherited
     }
     uint8_t *nout = a.noise_out + w * a.sites;
     NodeMeta *mout = a.meta_out + w * (a.npass + 1);
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(256) noise_kernel(const __grid_constant__ Nois
         mout[p] = par;
     __syncwarp();
     uint32_t mask = par.mask, phase = par.phase;
+    uint32_t noisy = 0;  // bit p: a Pauli was drawn at some site of pass p (passes >= 31 share bit 31)
     for (uint32_t b = 0; b < a.sites; b += 32) {
         const uint32_t s = b + lane;
         uint32_t xm = 0, yc = 0;
@@ -61,6 +63,12 @@ __global__ void __launch_bounds__(256) noise_kernel(const __grid_constant__ Nois
                 if (wb == 2) yc++;
             }
             nout[I.site] = (uint8_t)pz;  // the table runs in pass order; the noise row is by site
+            if (pz) {
+                uint32_t p = 0;  // entry s of the table belongs to pass p: pass_start[p] <= s < pass_start[p+1]
+                while (p + 1 < a.npass && a.pass_start[p + 1] <= s)
+                    p++;
+                noisy |= 1u << (p < 31u ? p : 31u);
+            }
         }
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -80,6 +88,13 @@ __global__ void __launch_bounds__(256) noise_kernel(const __grid_constant__ Nois
         mask ^= __shfl_sync(0xffffffffu, xm, 31);
         phase += __shfl_sync(0xffffffffu, yc, 31);
     }
+    // Flag, in bit 31 of the frame entry that opens it, every pass of this node
+    // with at least one Pauli: the pass kernels skip all noise checks of the others.
+    noisy = __reduce_or_sync(0xffffffffu, noisy);
+    __syncwarp();
+    for (uint32_t p = lane; p < a.npass; p += 32)
+        if ((noisy >> (p < 31u ? p : 31u)) & 1u)
+            mout[p].phase |= 0x80000000u;
 }
 
 int launch_noise(const NoiseLaunch &a, void *stream)

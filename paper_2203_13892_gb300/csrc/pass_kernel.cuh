@@ -231,6 +231,7 @@ __device__ uint64_t block_pick(uint64_t count, double target, F val, double *res
 // factor on a slot bit s (register index bit) goes to E[s]; slot-slot pairs go to
 // Gs.  Applying the block costs one complex product per amplitude.
 template <typename C, int NS> struct DiagAcc {
+    using V = C;  // a factor's value: the complex number itself
     C base;
     C E[NS > 0 ? NS : 1];
     C Gs[NS > 1 ? NS * (NS - 1) / 2 : 1];
@@ -251,6 +252,20 @@ template <typename C, int NS> struct DiagAcc {
         base_used = false;
         e_used = 0;
         gs_used = 0;
+    }
+    static __device__ __forceinline__ C minus_one() { return mk((decltype(C{}.x))-1, (decltype(C{}.x))0); }
+    __device__ __forceinline__ void mul_base(C f)
+    {
+        base = cmul(base, f);
+        base_used = true;
+    }
+    // a factor on fixed bits: applies to this thread iff `c`, but marks `base` as
+    // used on every thread so that the flush stays uniform
+    __device__ __forceinline__ void mul_base_if(bool c, C f)
+    {
+        base_used = true;
+        if (c)
+            base = cmul(base, f);
     }
     __device__ __forceinline__ void mul_E(int s, C f)
     {
@@ -278,30 +293,152 @@ template <typename C, int NS> struct DiagAcc {
     }
 };
 
+// FP32 states: every diagonal factor of the gates this library classes as
+// diagonal (Z, S, T, RZ, P, CZ, CP and their noise Z parts) has modulus one, so
+// the block is accumulated as a phase: an unsigned 32-bit fraction of a full
+// turn per accumulator (addition modulo 2^32 is addition of angles modulo 2 pi,
+// exact), and turned into complex factors only when the block is applied.
+// Compared with complex accumulators this halves the registers the block
+// holds (11 instead of 22 for 16 register slots) and replaces each factor's
+// complex product by one integer add.
+template <int NS> struct DiagAcc<float2, NS> {
+    using V = uint32_t;  // a factor's phase in units of 2^-32 turns
+    uint32_t base;
+    uint32_t E[NS > 0 ? NS : 1];
+    uint32_t Gs[NS > 1 ? NS * (NS - 1) / 2 : 1];
+    bool has_gs;
+    bool base_used;    // some factor went to `base` (uniform)
+    uint32_t e_used;   // slot factors that some gate touched (uniform)
+    uint32_t gs_used;  // slot pairs that some gate touched (uniform)
+    __device__ __forceinline__ void reset()
+    {
+        base = 0u;
+#pragma unroll
+        for (int s = 0; s < NS; s++)
+            E[s] = 0u;
+#pragma unroll
+        for (int i = 0; i < (NS > 1 ? NS * (NS - 1) / 2 : 1); i++)
+            Gs[i] = 0u;
+        has_gs = false;
+        base_used = false;
+        e_used = 0;
+        gs_used = 0;
+    }
+    static __device__ __forceinline__ uint32_t minus_one() { return 0x80000000u; }  // half a turn
+    __device__ __forceinline__ void mul_base(uint32_t f)
+    {
+        base += f;
+        base_used = true;
+    }
+    __device__ __forceinline__ void mul_base_if(bool c, uint32_t f)
+    {
+        base_used = true;
+        if (c)
+            base += f;
+    }
+    __device__ __forceinline__ void mul_E(int s, uint32_t f)
+    {
+        e_used |= 1u << s;
+        switch (s) {
+        case 0: if (NS > 0) E[0] += f; break;
+        case 1: if (NS > 1) E[NS > 1 ? 1 : 0] += f; break;
+        case 2: if (NS > 2) E[NS > 2 ? 2 : 0] += f; break;
+        case 3: if (NS > 3) E[NS > 3 ? 3 : 0] += f; break;
+        default: if (NS > 4) E[NS > 4 ? 4 : 0] += f; break;
+        }
+    }
+    __device__ __forceinline__ void mul_Gs(int s0, int s1, uint32_t f)
+    {
+        const int hi = s0 > s1 ? s0 : s1, lo = s0 > s1 ? s1 : s0;
+        const int idx = hi * (hi - 1) / 2 + lo;
+#pragma unroll
+        for (int k = 0; k < (NS > 1 ? NS * (NS - 1) / 2 : 1); k++)
+            if (k == idx)
+                Gs[k] += f;
+        has_gs = true;
+        gs_used |= 1u << idx;
+    }
+    // The frame mask bit of slot s flips (an X or Y drawn on that qubit) while
+    // phases are pending.  They were accumulated against the logical slot bit
+    // x_s of the old frame, which is 1 - y_s in the new one; substituting gives
+    // base += E_s, E_s -> -E_s, and for every pair (s, t): E_t += G_st,
+    // G_st -> -G_st.  So X noise needs no flush of the pending phases.
+    __device__ __forceinline__ void flip(int s)
+    {
+#pragma unroll
+        for (int q = 0; q < NS; q++) {
+            if (q != s)
+                continue;
+            if ((e_used >> q) & 1u) {
+                base += E[q];
+                base_used = true;
+                E[q] = 0u - E[q];
+            }
+#pragma unroll
+            for (int t = 0; t < NS; t++) {
+                if (t == q)
+                    continue;
+                const int hi = q > t ? q : t, lo = q > t ? t : q, idx = hi * (hi - 1) / 2 + lo;
+                if ((gs_used >> idx) & 1u) {
+                    E[t] += Gs[idx];
+                    e_used |= 1u << t;
+                    Gs[idx] = 0u - Gs[idx];
+                }
+            }
+        }
+    }
+};
+
+// exp(2 pi i a / 2^32) for a phase a in units of 2^-32 turns.  The angle is
+// rounded to 2^-23 turns (at most 3.7e-7 rad), taken into [-pi, pi) as a
+// signed integer, converted exactly with the 1.5 * 2^23 float trick, and passed
+// to the hardware sine and cosine (absolute error about 4e-7 on [-pi, pi]).
+__device__ __forceinline__ float2 expi_turn(uint32_t a)
+{
+    const int32_t ai = (int32_t)(a + 256u) >> 9;
+    const float f = __int_as_float(ai + 0x4B400000) - 12582912.0f;
+    float sn, cs;
+    __sincosf(f * 7.4901405e-07f, &sn, &cs);  // 2 pi / 2^23
+    return make_float2(cs, sn);
+}
+
+// Phase of a unit complex number in units of 2^-32 turns (rare paths only).
+__device__ __forceinline__ uint32_t turn_of(float re, float im)
+{
+    const double t = (double)atan2f(im, re) * (4294967296.0 / 6.283185307179586);
+    return (uint32_t)(int64_t)llrint(t);
+}
+
+// registers whose index has bit s set (NR = 2^LOGR registers)
+template <int LOGR> __device__ __forceinline__ constexpr uint32_t reg_pattern(int s)
+{
+    uint32_t m = 0;
+    for (int k = 0; k < (1 << LOGR); k++)
+        if ((k >> s) & 1)
+            m |= 1u << k;
+    return m;
+}
+
 // tile position j: thread bit (j < 8 or tile smaller than the CTA), slot bit s = j-8, or outside (0xff)
 __device__ __forceinline__ bool thread_or_outside(uint32_t j) { return j == 0xffu || j < 8u; }
 
 template <typename C, int NS>
-__device__ __forceinline__ void acc_alpha(DiagAcc<C, NS> &A, uint32_t j, uint32_t p, uint32_t xt, C f)
+__device__ __forceinline__ void acc_alpha(DiagAcc<C, NS> &A, uint32_t j, uint32_t p, uint32_t xt,
+                                          typename DiagAcc<C, NS>::V f)
 {
-    if (thread_or_outside(j)) {
-        A.base_used = true;
-        if ((xt >> p) & 1u)
-            A.base = cmul(A.base, f);
-    } else {
+    if (thread_or_outside(j))
+        A.mul_base_if(((xt >> p) & 1u) != 0u, f);
+    else
         A.mul_E((int)j - 8, f);
-    }
 }
 
 template <typename C, int NS>
 __device__ __forceinline__ void acc_gamma(DiagAcc<C, NS> &A, uint32_t j0, uint32_t p0, uint32_t j1, uint32_t p1,
-                                          uint32_t xt, C f)
+                                          uint32_t xt, typename DiagAcc<C, NS>::V f)
 {
     const bool a = thread_or_outside(j0), b = thread_or_outside(j1);
     if (a && b) {
-        A.base_used = true;
-        if ((xt >> p0) & (xt >> p1) & 1u)
-            A.base = cmul(A.base, f);
+        A.mul_base_if(((xt >> p0) & (xt >> p1) & 1u) != 0u, f);
     } else if (a) {
         if ((xt >> p0) & 1u)
             A.mul_E((int)j1 - 8, f);
@@ -391,6 +528,122 @@ __device__ __forceinline__ void acc_flush(DiagAcc<C, LOGR> &A, C (&v)[1 << LOGR]
                     if (((k >> hi) & 1) && ((k >> lo) & 1))
                         v[k] = cmul(v[k], Gb[hi * (hi - 1) / 2 + lo]);
             }
+    }
+    A.reset();
+}
+
+// v[k] *= exp(i a) on the registers whose index has bits HI and LO set (HI == LO:
+// one bit); nothing when a bit lies beyond the registers.
+template <int LOGR, int HI, int LO>
+__device__ __forceinline__ void apply_on_bits(float2 (&v)[1 << LOGR], uint32_t a)
+{
+    if constexpr (HI < LOGR && LO < LOGR) {
+        const float2 f = expi_turn(a);
+#pragma unroll
+        for (int k = 0; k < (1 << LOGR); k++)
+            if (((k >> HI) & 1) && ((k >> LO) & 1))
+                v[k] = cmul(v[k], f);
+    }
+}
+
+// FP32: multiply the NR register amplitudes by exp(i * phase(k)) where the
+// phase of register k is the accumulated quadratic form
+//   Q(x) = base + sum_s E_s x_s + sum_{s<t} G_st x_s x_t  at logical slot bits
+// x = k ^ msig.  With a frame mask the form is first rewritten in the register
+// bits b (x_s = 1 - b_s where m_s = 1): base' = Q(m), G'_st = -G_st when exactly
+// one of m_s, m_t is set, E'_s = (-1)^{m_s} (E_s + sum_{t != s, m_t} G_st).
+template <int LOGR>
+__device__ __forceinline__ void acc_flush(DiagAcc<float2, LOGR> &A, float2 (&v)[1 << LOGR], uint32_t msig)
+{
+    constexpr int NR = 1 << LOGR;
+    constexpr int NP = LOGR > 1 ? LOGR * (LOGR - 1) / 2 : 1;
+    uint32_t B = A.base;
+    uint32_t E[LOGR > 0 ? LOGR : 1], G[NP];
+#pragma unroll
+    for (int s = 0; s < LOGR; s++)
+        E[s] = A.E[s];
+#pragma unroll
+    for (int i = 0; i < NP; i++)
+        G[i] = A.Gs[i];
+    // Slot factors in use (uniform): those some gate touched and, under a frame
+    // mask, those a masked pair partner turns into linear ones.
+    uint32_t eu = A.e_used;
+#pragma unroll
+    for (int hi = 1; hi < LOGR; hi++)
+#pragma unroll
+        for (int lo = 0; lo < hi; lo++)
+            if ((A.gs_used >> (hi * (hi - 1) / 2 + lo)) & 1u) {
+                if ((msig >> hi) & 1u)
+                    eu |= 1u << lo;
+                if ((msig >> lo) & 1u)
+                    eu |= 1u << hi;
+            }
+    const bool bmul = A.base_used || (msig & eu) != 0u;  // base may differ from 0 (uniform)
+    if (msig != 0u) {
+        uint32_t En[LOGR > 0 ? LOGR : 1];
+#pragma unroll
+        for (int s = 0; s < LOGR; s++) {
+            const bool ms = (msig >> s) & 1u;
+            if (ms)
+                B += E[s];
+            uint32_t e = E[s];
+#pragma unroll
+            for (int t = 0; t < LOGR; t++) {
+                if (t == s)
+                    continue;
+                const int hi = s > t ? s : t, lo = s > t ? t : s;
+                if ((msig >> t) & 1u) {
+                    e += G[hi * (hi - 1) / 2 + lo];
+                    if (ms && t < s)
+                        B += G[hi * (hi - 1) / 2 + lo];
+                }
+            }
+            En[s] = ms ? 0u - e : e;
+        }
+#pragma unroll
+        for (int s = 0; s < LOGR; s++)
+            E[s] = En[s];
+#pragma unroll
+        for (int hi = 1; hi < LOGR; hi++)
+#pragma unroll
+            for (int lo = 0; lo < hi; lo++)
+                if (((msig >> hi) ^ (msig >> lo)) & 1u)
+                    G[hi * (hi - 1) / 2 + lo] = 0u - G[hi * (hi - 1) / 2 + lo];
+    }
+    // Apply as successive factors, each turned into a complex number once per
+    // thread (one sine/cosine each): the base on every register, a slot factor
+    // on the registers with that bit, a pair factor on those with both bits.
+    // Only the factors in use are visited (a loop over set bits with a switch,
+    // so that unused ones cost a branch, not predicated multiplies).
+    if (bmul) {
+        const float2 eb = expi_turn(B);
+#pragma unroll
+        for (int k = 0; k < NR; k++)
+            v[k] = cmul(v[k], eb);
+    }
+    for (uint32_t m = eu; m; m &= m - 1u) {
+        switch (__ffs(m) - 1) {
+        case 0: apply_on_bits<LOGR, 0, 0>(v, E[0]); break;
+        case 1: apply_on_bits<LOGR, 1, 1>(v, E[LOGR > 1 ? 1 : 0]); break;
+        case 2: apply_on_bits<LOGR, 2, 2>(v, E[LOGR > 2 ? 2 : 0]); break;
+        case 3: apply_on_bits<LOGR, 3, 3>(v, E[LOGR > 3 ? 3 : 0]); break;
+        default: apply_on_bits<LOGR, 4, 4>(v, E[LOGR > 4 ? 4 : 0]); break;
+        }
+    }
+    for (uint32_t m = A.gs_used; m; m &= m - 1u) {
+        // pair index hi(hi-1)/2 + lo
+        switch (__ffs(m) - 1) {
+        case 0: apply_on_bits<LOGR, 1, 0>(v, G[0]); break;
+        case 1: apply_on_bits<LOGR, 2, 0>(v, G[NP > 1 ? 1 : 0]); break;
+        case 2: apply_on_bits<LOGR, 2, 1>(v, G[NP > 2 ? 2 : 0]); break;
+        case 3: apply_on_bits<LOGR, 3, 0>(v, G[NP > 3 ? 3 : 0]); break;
+        case 4: apply_on_bits<LOGR, 3, 1>(v, G[NP > 4 ? 4 : 0]); break;
+        case 5: apply_on_bits<LOGR, 3, 2>(v, G[NP > 5 ? 5 : 0]); break;
+        case 6: apply_on_bits<LOGR, 4, 0>(v, G[NP > 6 ? 6 : 0]); break;
+        case 7: apply_on_bits<LOGR, 4, 1>(v, G[NP > 7 ? 7 : 0]); break;
+        case 8: apply_on_bits<LOGR, 4, 2>(v, G[NP > 8 ? 8 : 0]); break;
+        default: apply_on_bits<LOGR, 4, 3>(v, G[NP > 9 ? 9 : 0]); break;
+        }
     }
     A.reset();
 }
@@ -622,13 +875,30 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     uint8_t *nzs = reinterpret_cast<uint8_t *>(soff + 32);
     const bool nz_staged = a.sites <= (uint32_t)kNoiseStage;
     uint8_t *pbuf = nzs + ((a.sites < (uint32_t)kNoiseStage ? a.sites : (uint32_t)kNoiseStage) + 15u) / 16u * 16u;
-    if (nz_staged)
+    // passes in which this node drew no Pauli (most of them) skip every noise check
+    const bool pnoisy = (m0.phase & kMetaNoisy) != 0u;
+    if (nz_staged && pnoisy)
         for (uint32_t x = tid; x < a.sites; x += kThreads)
             nzs[x] = nzg[x];
     auto noise_at = [&](uint32_t site) -> uint32_t { return nz_staged ? nzs[site] : nzg[site]; };
 
-    DiagAcc<C, LOGR> acc;
+    using Acc = DiagAcc<C, LOGR>;
+    using V = typename Acc::V;  // a diagonal factor: complex (FP64) or a phase in 2^-32 turns (FP32)
+    Acc acc;
     acc.reset();
+    // a factor value of the compiled program / a per-gate matrix entry
+    auto fv_mat = [&](R re, R im) -> V {
+        if constexpr (sizeof(R) == 4)
+            return turn_of(re, im);
+        else
+            return mk(re, im);
+    };
+    auto fv_is_one = [&](V f) -> bool {
+        if constexpr (sizeof(R) == 4)
+            return f == 0u;
+        else
+            return f.x == (R)1 && f.y == (R)0;
+    };
     bool pending = false;
     auto slot_mask = [&]() {
         uint32_t m = 0;
@@ -639,7 +909,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     };
     auto flush = [&]() {
         if (pending) {
-            acc_flush<C, LOGR>(acc, v, slot_mask());
+            acc_flush(acc, v, slot_mask());
             pending = false;
         }
     };
@@ -648,7 +918,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     auto apply_noise = [&](uint32_t pz, uint32_t npaulis, uint32_t j0, uint32_t p0, uint32_t j1, uint32_t p1) {
         const uint32_t wa = npaulis == 15 ? (pz >> 2) : pz;
         const uint32_t wb = npaulis == 15 ? (pz & 3u) : 0u;
-        const C minus = mk((R)-1, (R)0);
+        const V minus = Acc::minus_one();
         if (wa >= 2) {
             acc_alpha(acc, j0, p0, xt, minus);
             pending = true;
@@ -657,15 +927,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
             acc_alpha(acc, j1, p1, xt, minus);
             pending = true;
         }
-        const uint32_t xm = ((wa == 1 || wa == 2) ? (1u << p0) : 0u) | ((wb == 1 || wb == 2) ? (1u << p1) : 0u);
+        const bool xa = wa == 1 || wa == 2, xb = wb == 1 || wb == 2;
+        const uint32_t xm = (xa ? (1u << p0) : 0u) | (xb ? (1u << p1) : 0u);
         if (xm) {
-            flush();
+            if constexpr (sizeof(R) == 4) {
+                if (xa && !thread_or_outside(j0))
+                    acc.flip((int)j0 - 8);
+                if (xb && !thread_or_outside(j1))
+                    acc.flip((int)j1 - 8);
+            } else {
+                flush();
+            }
             mask ^= xm;
             xt ^= xm;
         }
     };
     auto dense1 = [&](uint32_t j, uint32_t p, C u00, C u01, C u10, C u11) {
-        flush();
+        // the caller has applied the pending diagonal phases
         if ((mask >> p) & 1u) {  // frame conjugation U'[r][c] = U[r^1][c^1]
             const C t0 = u00, t1 = u01;
             u00 = u11;
@@ -704,7 +982,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     };
     // real 2x2 matrix (H, RY, X, ...): half the multiplies
     auto dense1_real = [&](uint32_t j, uint32_t p, R u00, R u01, R u10, R u11) {
-        flush();
+        // the caller has applied the pending diagonal phases
         if ((mask >> p) & 1u) {
             const R t0 = u00, t1 = u01;
             u00 = u11;
@@ -743,7 +1021,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     };
     // U: 16 complex values, row-major, read through `get`
     auto dense2 = [&](uint32_t j0, uint32_t j1, uint32_t p0, uint32_t p1, auto get) {
-        flush();
+        // the caller has applied the pending diagonal phases
         const uint32_t mu = ((mask >> p0) & 1u) | (((mask >> p1) & 1u) << 1);
         __syncthreads();
         if (active) {
@@ -773,17 +1051,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     auto diag_gate = [&](const Instr &I) {
         const R *M = mats + (size_t)I.gate * 32;
         const uint32_t fl = I.pad;
-        if (fl & 1u) {
-            acc.base = cmul(acc.base, mk(M[0], M[1]));
-            acc.base_used = true;
-        }
+        if (fl & 1u)
+            acc.mul_base(fv_mat(M[0], M[1]));
         if (fl & 2u)
-            acc_alpha(acc, I.j0, I.p0, xt, mk(M[2], M[3]));
+            acc_alpha(acc, I.j0, I.p0, xt, fv_mat(M[2], M[3]));
         if (I.op == OP_DIAG2) {
             if (fl & 4u)
-                acc_alpha(acc, I.j1, I.p1, xt, mk(M[4], M[5]));
+                acc_alpha(acc, I.j1, I.p1, xt, fv_mat(M[4], M[5]));
             if (fl & 8u)
-                acc_gamma(acc, I.j0, I.p0, I.j1, I.p1, xt, mk(M[6], M[7]));
+                acc_gamma(acc, I.j0, I.p0, I.j1, I.p1, xt, fv_mat(M[6], M[7]));
         }
         pending = true;
     };
@@ -927,18 +1203,30 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                 const uint32_t hibeg = hw.z, hiend = hw.w;
                 const unsigned char *pay = pbuf + p + 16;
                 auto pc = [&](uint32_t i) -> C { return *reinterpret_cast<const C *>(pay + i * CS); };
+                // The one place pending diagonal phases are applied (FP32; FP64 also
+                // flushes at X noise): before every record that is not a diagonal run,
+                // the end-of-pass record included.  A single call site keeps the
+                // kernel's code small.
+                if (sizeof(R) == 4 && MODE != MODE_STORE && htype == REC_END) {
+                    acc.reset();  // a final diagonal run changes phases only, not the measured |a|^2
+                    pending = false;
+                }
+                if (htype != REC_RUN)
+                    flush();
+                if (htype == REC_END)
+                    break;
                 if (htype == REC_DENSE1) {
                     if (hc)
                         dense1_real(ha, hb, pc(0).x, pc(1).x, pc(2).x, pc(3).x);
                     else
                         dense1(ha, hb, pc(0), pc(1), pc(2), pc(3));
-                    const uint32_t pz = noise_at(hsite);
+                    const uint32_t pz = pnoisy ? noise_at(hsite) : 0u;
                     if (pz)
                         apply_noise(pz, 3, ha, hb, ha, hb);
                     p += 16u + ((4u * CS + 15u) & ~15u);
                 } else if (htype == REC_DENSE2) {
                     dense2(ha, hb, hc, hd, pc);
-                    const uint32_t pz = noise_at(hsite);
+                    const uint32_t pz = pnoisy ? noise_at(hsite) : 0u;
                     if (pz)
                         apply_noise(pz, 15, ha, hc, hb, hd);
                     p += 16u + 16u * CS;
@@ -948,13 +1236,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                         atomicOr(a.err, 2u);
                   } else {
                     uint32_t anyf = 0;  // the block's gates need not have consecutive sites
-                    for (uint32_t x = hibeg + (tid & 31u); x < hiend; x += 32u)
+                    for (uint32_t x = hibeg + (tid & 31u); pnoisy && x < hiend; x += 32u)
                         anyf |= noise_at(a.instr[x].site);
                     const bool any = __any_sync(0xffffffffu, anyf != 0u);
                     bool done = tc_failed;  // after a failed wait nothing more is computed
                     if constexpr (sizeof(R) == 4) {
                         if (!done && !any && a.fused_k == ha) {
-                            flush();
                             fused_apply(pay, ha);
                             done = true;
                         }
@@ -964,8 +1251,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                             const Instr I = a.instr[ii];
                             const R *M = mats + (size_t)I.gate * 32;
                             if (I.op == OP_DENSE1) {
+                                flush();
                                 dense1(I.j0, I.p0, mk(M[0], M[1]), mk(M[2], M[3]), mk(M[4], M[5]), mk(M[6], M[7]));
                             } else if (I.op == OP_DENSE2) {
+                                flush();
                                 dense2(I.j0, I.j1, I.p0, I.p1, [&](uint32_t kk) { return mk(M[2 * kk], M[2 * kk + 1]); });
                             } else if (I.op == OP_DIAG1 || I.op == OP_DIAG2) {
                                 diag_gate(I);
@@ -977,32 +1266,110 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                     }
                   }
                     p += 48u;
+                } else if constexpr (sizeof(R) == 4) {
+                    // FP32 run: phases grouped by accumulator (RunHdr32), no per-factor
+                    // dispatch; a node with a Pauli inside the run goes gate by gate
+                    const RunHdr32 &rh = *reinterpret_cast<const RunHdr32 *>(pay);
+                    uint32_t nent = rh.nbase;
+#pragma unroll
+                    for (int q = 0; q < (int)kMaxSlots; q++)
+                        nent += rh.ne[q];
+                    constexpr uint32_t ES = 16u + 4u * (uint32_t)sizeof(V);  // GateEnt + 4 phases
+                    const unsigned char *gents = pay + 80 + (nent * 8u + 15u) / 16u * 16u;
+                    const uint32_t ngates = hiend - hibeg;
+                    uint32_t anyn = 0;
+                    for (uint32_t x = tid & 31u; pnoisy && x < ngates; x += 32u)
+                        anyn |= noise_at(*reinterpret_cast<const uint32_t *>(gents + x * ES + 12));
+                    if (!__any_sync(0xffffffffu, anyn != 0u)) {
+                        if (rh.g0)
+                            acc.mul_base(rh.g0);
+                        const uint2 *en = reinterpret_cast<const uint2 *>(pay + 80);
+                        const uint32_t nb = rh.nbase;
+                        if (nb) {
+                            acc.base_used = true;
+                            uint32_t add = 0;
+                            for (uint32_t i = 0; i < nb; i++) {
+                                const uint2 e = en[i];
+                                if ((xt & e.x) == e.x)
+                                    add += e.y;
+                            }
+                            acc.base += add;
+                            en += nb;
+                        }
+#pragma unroll
+                        for (int q = 0; q < LOGR; q++) {
+                            const uint32_t nq = rh.ne[q];
+                            if (nq == 0u && !((rh.eused >> q) & 1u))
+                                continue;
+                            uint32_t add = rh.econst[q];
+                            for (uint32_t i = 0; i < nq; i++) {
+                                const uint2 e = en[i];
+                                if ((xt & e.x) == e.x)
+                                    add += e.y;
+                            }
+                            en += nq;
+                            acc.E[q] += add;
+                            acc.e_used |= 1u << q;
+                        }
+                        if (rh.gused) {
+#pragma unroll
+                            for (int i = 0; i < (LOGR > 1 ? LOGR * (LOGR - 1) / 2 : 1); i++)
+                                if ((rh.gused >> i) & 1u)
+                                    acc.Gs[i] += rh.gp[i];
+                            acc.gs_used |= rh.gused;
+                            acc.has_gs = true;
+                        }
+                        pending = true;
+                    } else {  // gate by gate from the entries after the factors
+                        const unsigned char *gq = gents;
+                        for (uint32_t ii = 0; ii < ngates; ii++, gq += ES) {
+                            const uint4 e = *reinterpret_cast<const uint4 *>(gq);
+                            const uint32_t op = e.x & 0xffu, fl = (e.x >> 8) & 0xffu, j0 = (e.x >> 16) & 0xffu,
+                                           p0 = e.x >> 24, j1 = e.y & 0xffu, p1 = (e.y >> 8) & 0xffu,
+                                           np0 = (e.y >> 16) & 0xffu, np1 = e.y >> 24, npl = e.z & 0xffu;
+                            const V *M = reinterpret_cast<const V *>(gq + 16);
+                            if (op == OP_DIAG1 || op == OP_DIAG2) {
+                                if (fl & 1u)
+                                    acc.mul_base(M[0]);
+                                if (fl & 2u)
+                                    acc_alpha(acc, j0, p0, xt, M[1]);
+                                if (op == OP_DIAG2) {
+                                    if (fl & 4u)
+                                        acc_alpha(acc, j1, p1, xt, M[2]);
+                                    if (fl & 8u)
+                                        acc_gamma(acc, j0, p0, j1, p1, xt, M[3]);
+                                }
+                                pending = true;
+                            }
+                            const uint32_t pz = noise_at(e.w);
+                            if (pz)
+                                apply_noise(pz, npl, j0, np0, j1, np1);
+                        }
+                    }
+                    p += 96u + (nent * 8u + 15u) / 16u * 16u + ngates * ES;
                 } else {
                     const uint32_t nfac = ha + hb + hc + hd + he;
-                    constexpr uint32_t ES = 16u + 4u * CS;  // GateEnt + 4 factors
+                    constexpr uint32_t ES = 16u + 4u * (uint32_t)sizeof(V);  // GateEnt + 4 factors
                     const unsigned char *gents = pay + 16 + nfac * (CS == 8 ? 16u : 32u);
                     const uint32_t ngates = hiend - hibeg;
                     uint32_t anyn = 0;  // a Pauli at any site of the run? (the lanes split the gates)
-                    for (uint32_t x = tid & 31u; x < ngates; x += 32u)
+                    for (uint32_t x = tid & 31u; pnoisy && x < ngates; x += 32u)
                         anyn |= noise_at(*reinterpret_cast<const uint32_t *>(gents + x * ES + 12));
                     if (!__any_sync(0xffffffffu, anyn != 0u)) {
-                        const C g0 = pc(0);
-                        if (g0.x != (R)1 || g0.y != (R)0) {
-                            acc.base = cmul(acc.base, g0);
-                            acc.base_used = true;
-                        }
+                        const V g0 = *reinterpret_cast<const V *>(pay);
+                        if (!fv_is_one(g0))
+                            acc.mul_base(g0);
                         if (ha + hc)
                             acc.base_used = true;
                         const unsigned char *fp = pay + 16;
                         constexpr uint32_t FS = CS == 8 ? 16u : 32u;
-                        auto fval = [&](const unsigned char *q) -> C {
-                            return *reinterpret_cast<const C *>(q + (CS == 8 ? 8 : 16));
+                        auto fval = [&](const unsigned char *q) -> V {
+                            return *reinterpret_cast<const V *>(q + (CS == 8 ? 8 : 16));
                         };
                         // FacHdr as one 64-bit word: kind | j0<<8 | p0<<16 | j1<<24 | p1<<32
                         for (uint32_t f = 0; f < ha; f++, fp += FS) {  // a^{x_p}, p fixed
                             const uint32_t w0 = *reinterpret_cast<const uint32_t *>(fp);
-                            if ((xt >> ((w0 >> 16) & 0xffu)) & 1u)
-                                acc.base = cmul(acc.base, fval(fp));
+                            acc.mul_base_if(((xt >> ((w0 >> 16) & 0xffu)) & 1u) != 0u, fval(fp));
                         }
                         for (uint32_t f = 0; f < hb; f++, fp += FS) {  // a^{x_s}, slot s
                             const uint32_t w0 = *reinterpret_cast<const uint32_t *>(fp);
@@ -1010,8 +1377,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                         }
                         for (uint32_t f = 0; f < hc; f++, fp += FS) {  // c^{x_p0 x_p1}, both fixed
                             const uint2 w = *reinterpret_cast<const uint2 *>(fp);
-                            if ((xt >> ((w.x >> 16) & 0xffu)) & (xt >> (w.y & 0xffu)) & 1u)
-                                acc.base = cmul(acc.base, fval(fp));
+                            acc.mul_base_if(((xt >> ((w.x >> 16) & 0xffu)) & (xt >> (w.y & 0xffu)) & 1u) != 0u,
+                                            fval(fp));
                         }
                         for (uint32_t f = 0; f < hd; f++, fp += FS) {  // c^{x_p0 x_s1}
                             const uint32_t w0 = *reinterpret_cast<const uint32_t *>(fp);
@@ -1030,12 +1397,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                             const uint32_t op = e.x & 0xffu, fl = (e.x >> 8) & 0xffu, j0 = (e.x >> 16) & 0xffu,
                                            p0 = e.x >> 24, j1 = e.y & 0xffu, p1 = (e.y >> 8) & 0xffu,
                                            np0 = (e.y >> 16) & 0xffu, np1 = e.y >> 24, npl = e.z & 0xffu;
-                            const C *M = reinterpret_cast<const C *>(gq + 16);
+                            const V *M = reinterpret_cast<const V *>(gq + 16);
                             if (op == OP_DIAG1 || op == OP_DIAG2) {
-                                if (fl & 1u) {
-                                    acc.base = cmul(acc.base, M[0]);
-                                    acc.base_used = true;
-                                }
+                                if (fl & 1u)
+                                    acc.mul_base(M[0]);
                                 if (fl & 2u)
                                     acc_alpha(acc, j0, p0, xt, M[1]);
                                 if (op == OP_DIAG2) {
@@ -1055,7 +1420,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                 }
             }
         }
-        flush();
     } else {
         mask = m1.mask;
     }

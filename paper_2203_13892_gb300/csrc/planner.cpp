@@ -461,10 +461,19 @@ static void sink_diagonals(PlanHost &P)
 #ifndef TQS_FUSE_MIN_DENSE
 #define TQS_FUSE_MIN_DENSE 2  // dense gates a block needs before it is fused onto the tensor cores
 #endif
+// A unit complex number as a phase in units of 2^-32 turns (rounded), the form
+// in which FP32 programs carry diagonal factors.
+static uint32_t turn32(std::complex<double> z)
+{
+    const double t = std::arg(z) / (2.0 * M_PI);  // (-1/2, 1/2]
+    return (uint32_t)(int64_t)std::llround(t * 4294967296.0);
+}
+
 static void compile_programs(PlanHost &P)
 {
     const bool f64 = P.prec == TQS_FP64;
-    const size_t csz = f64 ? 16 : 8, fsz = f64 ? 32 : 16, esz = 16 + 4 * csz;
+    // FP64: diagonal factors are complex doubles; FP32: phases (turn32), 4 bytes
+    const size_t csz = f64 ? 16 : 8, fsz = f64 ? 32 : 16, esz = 16 + 4 * (f64 ? csz : 4);
     const size_t kMaxFactors = 200;
     std::vector<uint8_t> &out = P.prog;
     out.clear();
@@ -488,6 +497,15 @@ static void compile_programs(PlanHost &P)
         while (out.size() % 16)
             out.push_back(0);
     };
+    // a diagonal factor in the program's form
+    auto putd = [&](std::complex<double> z) {
+        if (f64) {
+            putc(z);
+        } else {
+            const uint32_t a = turn32(z);
+            put(&a, 4);
+        }
+    };
     auto cplx = [&](uint32_t gate, int k) {
         return std::complex<double>(P.mats64[(size_t)gate * 32 + 2 * k], P.mats64[(size_t)gate * 32 + 2 * k + 1]);
     };
@@ -506,10 +524,8 @@ static void compile_programs(PlanHost &P)
         auto is_slot = [&](uint8_t p) { return pos[p] != 0xff && pos[p] >= 8; };
         ps.chunk_begin = (uint32_t)P.chunk_off.size();
         ps.fused_blocks = 0;
-        if (ps.ibeg < ps.iend) {
-            P.chunk_off.push_back((uint32_t)out.size());
-            chunk_start = out.size();
-        }
+        P.chunk_off.push_back((uint32_t)out.size());
+        chunk_start = out.size();
         // tensor-core fusion: FP32 states and tiles with 128 columns beside k = t - 7 fused qubits
         const uint32_t kf = (P.fuse && !f64 && (ps.t == 11 || ps.t == 12)) ? ps.t - 7 : 0;
         uint32_t k = ps.ibeg;
@@ -673,6 +689,61 @@ static void compile_programs(PlanHost &P)
             std::stable_sort(facs.begin(), facs.end(),
                              [](const std::pair<FacHdr, std::complex<double>> &x,
                                 const std::pair<FacHdr, std::complex<double>> &y) { return x.first.kind < y.first.kind; });
+            if (!f64) {
+                // FP32 runs: the factors grouped by the phase accumulator they feed,
+                // each with the mask of fixed physical bits whose logical values
+                // must all be 1 for it to apply (one or two bits), and the uniform
+                // ones (slot-only) summed here.  See RunHdr32.
+                std::vector<std::pair<uint32_t, uint32_t>> lists[1 + kMaxSlots];
+                uint32_t econst[kMaxSlots] = {0}, gp[kMaxSlots * (kMaxSlots - 1) / 2] = {0};
+                uint32_t eused = 0, gused = 0;
+                for (auto &f : facs) {
+                    const FacHdr &fh = f.first;
+                    const uint32_t ang = turn32(f.second);
+                    switch (fh.kind) {
+                    case FAC_A_FIXED: lists[0].push_back({1u << fh.p0, ang}); break;
+                    case FAC_C_FIXED: lists[0].push_back({(1u << fh.p0) | (1u << fh.p1), ang}); break;
+                    case FAC_A_SLOT: econst[fh.j0 - 8] += ang; eused |= 1u << (fh.j0 - 8); break;
+                    case FAC_C_MIXED: lists[1 + fh.j1 - 8].push_back({1u << fh.p0, ang}); break;
+                    default: {  // FAC_C_SLOTS
+                        const uint32_t a = fh.j0 - 8u, b = fh.j1 - 8u, hi = a > b ? a : b, lo = a > b ? b : a;
+                        gp[hi * (hi - 1) / 2 + lo] += ang;
+                        gused |= 1u << (hi * (hi - 1) / 2 + lo);
+                    }
+                    }
+                }
+                size_t nent = 0;
+                for (auto &l : lists)
+                    nent += l.size();
+                const size_t body = 16 + 16 + 64 + (nent * 8 + 15) / 16 * 16 + (size_t)(k - r0) * esz;
+                reserve(body);
+                RecHdr h;
+                std::memset(&h, 0, sizeof(h));
+                h.type = REC_RUN;
+                h.site = P.prog_instrs[r0].site;
+                h.ibeg = r0;
+                h.iend = k;
+                put(&h, 16);
+                RunHdr32 rh;
+                std::memset(&rh, 0, sizeof(rh));
+                rh.nbase = (uint8_t)lists[0].size();
+                for (uint32_t q = 0; q < kMaxSlots; q++)
+                    rh.ne[q] = (uint8_t)lists[1 + q].size();
+                rh.gused = (uint16_t)gused;
+                rh.eused = (uint8_t)eused;
+                rh.g0 = turn32(G);
+                for (uint32_t q = 0; q < kMaxSlots; q++)
+                    rh.econst[q] = econst[q];
+                for (uint32_t q = 0; q < kMaxSlots * (kMaxSlots - 1) / 2; q++)
+                    rh.gp[q] = gp[q];
+                put(&rh, sizeof(rh));
+                for (auto &l : lists)
+                    for (auto &e : l) {
+                        put(&e.first, 4);
+                        put(&e.second, 4);
+                    }
+                pad16();
+            } else {
             uint8_t cnt[8] = {0};
             for (auto &f : facs)
                 cnt[f.first.kind]++;
@@ -689,15 +760,16 @@ static void compile_programs(PlanHost &P)
             h.ibeg = r0;
             h.iend = k;
             put(&h, 16);
-            putc(G);
+            putd(G);
             pad16();
             for (auto &f : facs) {
                 put(&f.first, 8);
                 if (f64)
                     out.insert(out.end(), 8, 0);  // the value sits 16-byte aligned
-                putc(f.second);
+                putd(f.second);
+                pad16();
             }
-            pad16();
+            }
             // the run gate by gate, for nodes with a Pauli inside it (see GateEnt)
             for (uint32_t x = r0; x < k; x++) {
                 const Instr &d = P.prog_instrs[x];
@@ -715,9 +787,15 @@ static void compile_programs(PlanHost &P)
                 g.site = d.site;
                 put(&g, 16);
                 for (int e = 0; e < 4; e++)
-                    putc(d.op == OP_DIAG1 || d.op == OP_DIAG2 ? cplx(d.gate, e) : std::complex<double>(1.0, 0.0));
+                    putd(d.op == OP_DIAG1 || d.op == OP_DIAG2 ? cplx(d.gate, e) : std::complex<double>(1.0, 0.0));
             }
         }
+        reserve(16);
+        RecHdr endh;
+        std::memset(&endh, 0, sizeof(endh));
+        endh.type = REC_END;
+        endh.ibeg = endh.iend = ps.iend;
+        put(&endh, 16);
         ps.chunk_end = (uint32_t)P.chunk_off.size();
     }
     P.chunk_off.push_back((uint32_t)out.size());
