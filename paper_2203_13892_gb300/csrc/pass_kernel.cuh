@@ -532,17 +532,22 @@ __device__ __forceinline__ void acc_flush(DiagAcc<C, LOGR> &A, C (&v)[1 << LOGR]
     A.reset();
 }
 
-// v[k] *= exp(i a) on the registers whose index has bits HI and LO set (HI == LO:
-// one bit); nothing when a bit lies beyond the registers.
-template <int LOGR, int HI, int LO>
-__device__ __forceinline__ void apply_on_bits(float2 (&v)[1 << LOGR], uint32_t a)
+// v[k] *= exp(i B) on the registers without bit S, exp(i (B + Es)) on those with it.
+template <int LOGR, int S>
+__device__ __forceinline__ void apply_one_slot(float2 (&v)[1 << LOGR], uint32_t B, uint32_t Es, bool bmul)
 {
-    if constexpr (HI < LOGR && LO < LOGR) {
-        const float2 f = expi_turn(a);
+    if constexpr (S < LOGR) {
+        const float2 f1 = expi_turn(B + Es);
+        float2 f0 = make_float2(1.0f, 0.0f);
+        if (bmul)
+            f0 = expi_turn(B);
 #pragma unroll
-        for (int k = 0; k < (1 << LOGR); k++)
-            if (((k >> HI) & 1) && ((k >> LO) & 1))
-                v[k] = cmul(v[k], f);
+        for (int k = 0; k < (1 << LOGR); k++) {
+            if ((k >> S) & 1)
+                v[k] = cmul(v[k], f1);
+            else if (bmul)
+                v[k] = cmul(v[k], f0);
+        }
     }
 }
 
@@ -610,39 +615,44 @@ __device__ __forceinline__ void acc_flush(DiagAcc<float2, LOGR> &A, float2 (&v)[
                 if (((msig >> hi) ^ (msig >> lo)) & 1u)
                     G[hi * (hi - 1) / 2 + lo] = 0u - G[hi * (hi - 1) / 2 + lo];
     }
-    // Apply as successive factors, each turned into a complex number once per
-    // thread (one sine/cosine each): the base on every register, a slot factor
-    // on the registers with that bit, a pair factor on those with both bits.
-    // Only the factors in use are visited (a loop over set bits with a switch,
-    // so that unused ones cost a branch, not predicated multiplies).
-    if (bmul) {
-        const float2 eb = expi_turn(B);
+    // Apply.  Without slot terms every register takes the thread's base phase:
+    // one sine/cosine and a multiply per register.  With slot terms each
+    // register's whole phase is summed in integers and turned into its factor
+    // on its own: 2^LOGR independent chains, so the hardware sine/cosine and the
+    // multiplies of different registers overlap instead of waiting on one
+    // another factor by factor.
+    if (eu == 0u && A.gs_used == 0u) {
+        if (bmul) {
+            const float2 eb = expi_turn(B);
 #pragma unroll
-        for (int k = 0; k < NR; k++)
-            v[k] = cmul(v[k], eb);
-    }
-    for (uint32_t m = eu; m; m &= m - 1u) {
-        switch (__ffs(m) - 1) {
-        case 0: apply_on_bits<LOGR, 0, 0>(v, E[0]); break;
-        case 1: apply_on_bits<LOGR, 1, 1>(v, E[LOGR > 1 ? 1 : 0]); break;
-        case 2: apply_on_bits<LOGR, 2, 2>(v, E[LOGR > 2 ? 2 : 0]); break;
-        case 3: apply_on_bits<LOGR, 3, 3>(v, E[LOGR > 3 ? 3 : 0]); break;
-        default: apply_on_bits<LOGR, 4, 4>(v, E[LOGR > 4 ? 4 : 0]); break;
+            for (int k = 0; k < NR; k++)
+                v[k] = cmul(v[k], eb);
         }
-    }
-    for (uint32_t m = A.gs_used; m; m &= m - 1u) {
-        // pair index hi(hi-1)/2 + lo
-        switch (__ffs(m) - 1) {
-        case 0: apply_on_bits<LOGR, 1, 0>(v, G[0]); break;
-        case 1: apply_on_bits<LOGR, 2, 0>(v, G[NP > 1 ? 1 : 0]); break;
-        case 2: apply_on_bits<LOGR, 2, 1>(v, G[NP > 2 ? 2 : 0]); break;
-        case 3: apply_on_bits<LOGR, 3, 0>(v, G[NP > 3 ? 3 : 0]); break;
-        case 4: apply_on_bits<LOGR, 3, 1>(v, G[NP > 4 ? 4 : 0]); break;
-        case 5: apply_on_bits<LOGR, 3, 2>(v, G[NP > 5 ? 5 : 0]); break;
-        case 6: apply_on_bits<LOGR, 4, 0>(v, G[NP > 6 ? 6 : 0]); break;
-        case 7: apply_on_bits<LOGR, 4, 1>(v, G[NP > 7 ? 7 : 0]); break;
-        case 8: apply_on_bits<LOGR, 4, 2>(v, G[NP > 8 ? 8 : 0]); break;
-        default: apply_on_bits<LOGR, 4, 3>(v, G[NP > 9 ? 9 : 0]); break;
+    } else if (A.gs_used == 0u && (eu & (eu - 1u)) == 0u) {
+        // one slot term: the registers without the bit take the base phase, those
+        // with it the base plus the slot's phase (two sines/cosines)
+        switch (__ffs(eu) - 1) {
+        case 0: apply_one_slot<LOGR, 0>(v, B, E[0], bmul); break;
+        case 1: apply_one_slot<LOGR, 1>(v, B, E[LOGR > 1 ? 1 : 0], bmul); break;
+        case 2: apply_one_slot<LOGR, 2>(v, B, E[LOGR > 2 ? 2 : 0], bmul); break;
+        case 3: apply_one_slot<LOGR, 3>(v, B, E[LOGR > 3 ? 3 : 0], bmul); break;
+        default: apply_one_slot<LOGR, 4>(v, B, E[LOGR > 4 ? 4 : 0], bmul); break;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NR; k++) {
+            uint32_t a = B;
+#pragma unroll
+            for (int sb = 0; sb < LOGR; sb++)
+                if ((k >> sb) & 1)
+                    a += E[sb];
+#pragma unroll
+            for (int hi = 1; hi < LOGR; hi++)
+#pragma unroll
+                for (int lo = 0; lo < hi; lo++)
+                    if (((k >> hi) & 1) && ((k >> lo) & 1))
+                        a += G[hi * (hi - 1) / 2 + lo];
+            v[k] = cmul(v[k], expi_turn(a));
         }
     }
     A.reset();
@@ -693,7 +703,7 @@ template <typename C> __device__ __forceinline__ C shfl_xor_c(C a, int m)
 }
 
 #ifndef TQS_FP32_MIN_CTAS
-#define TQS_FP32_MIN_CTAS 3  // resident CTAs per SM asked of ptxas for FP32 tiles of 2^12 amplitudes
+#define TQS_FP32_MIN_CTAS 4  // resident CTAs per SM asked of ptxas for FP32 tiles of 2^12 amplitudes
 #endif
 // FUSE: the pass holds REC_FUSED records (FP32 tiles of 2^11 or 2^12 only); a
 // separate instantiation so that the tensor-core code does not weigh on the
@@ -1435,8 +1445,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
 
     // ---- epilogue ------------------------------------------------------
     if (MODE == MODE_STORE) {
+        C *dst = reinterpret_cast<C *>(a.out) + (uint64_t)slot * a.state_elems;
         if (active) {
-            C *dst = reinterpret_cast<C *>(a.out) + (uint64_t)slot * a.state_elems;
             const uint32_t tb0 = base | tphys;
 #pragma unroll
             for (int k = 0; k < NR; k++)
