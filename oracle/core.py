@@ -74,6 +74,14 @@ def lib():
             L.orc_leaf_outcome.restype = C.c_int64
             L.orc_node_noise.argtypes = [C.c_int, ip, C.c_double, C.c_double, C.c_uint64, ip, C.c_int, C.c_uint64, ip]
             L.orc_max_threads.restype = C.c_int
+            L.orc_run_tree_k.argtypes = circ + [C.c_double] * 3 + [dp, C.c_uint64, C.c_uint64, C.c_int, u64p, ip, C.c_int, u64p]
+            L.orc_run_tree_k.restype = C.c_int
+            L.orc_node_state_k.argtypes = circ + [C.c_double, C.c_double, dp, C.c_uint64, C.c_int, u64p, ip, C.c_int, C.c_uint64, dp]
+            L.orc_node_state_k.restype = C.c_int
+            L.orc_leaf_outcome_k.argtypes = circ + [C.c_double] * 3 + [dp, C.c_uint64, C.c_int, u64p, ip, C.c_uint64]
+            L.orc_leaf_outcome_k.restype = C.c_int64
+            L.orc_thermal_params.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp]
+            L.orc_thermal_params.restype = C.c_int
             _lib = L
     return _lib
 
@@ -160,39 +168,72 @@ def ideal_state(circuit) -> np.ndarray:
     return out[0::2] + 1j * out[1::2]
 
 
+def thermal_params(t1: float, t2: float, t: float):
+    """(gamma, lambda) of the amplitude damping and phase damping that make up
+    thermal relaxation over a gate of duration t (T2 <= 2 T1)."""
+    g, l = C.c_double(), C.c_double()
+    if lib().orc_thermal_params(t1, t2, t, C.byref(g), C.byref(l)) != 0:
+        raise ValueError("thermal relaxation needs T1 > 0, 0 < T2 <= 2 T1 and t >= 0")
+    return g.value, l.value
+
+
+def kraus_params(ad: float = 0.0, pd: float = 0.0, t1: float = 0.0, t2: float = 0.0,
+                 time_1q: float = 0.0, time_2q: float = 0.0) -> np.ndarray:
+    """The oracle's channel array: [AD gamma, PD lambda, TR gamma/lambda after a
+    one-qubit gate, TR gamma/lambda after a two-qubit gate] (zeros: no channel)."""
+    kr = np.zeros(6)
+    kr[0], kr[1] = ad, pd
+    if t1 > 0.0:
+        kr[2], kr[3] = thermal_params(t1, t2, time_1q)
+        kr[4], kr[5] = thermal_params(t1, t2, time_2q)
+    return kr
+
+
+def _kr(kraus):
+    if kraus is None:
+        return None
+    k = np.ascontiguousarray(kraus, dtype=np.float64)
+    assert k.shape == (6,)
+    return k
+
+
 def run_tree(circuit, p1: float, p2: float, pm: float, shots: int, seed: int,
-             arity: Sequence[int], split: Sequence[int], threads: int = 0) -> np.ndarray:
-    """Histogram (uint64[2^n]) of the tree Monte-Carlo; ``arity=[N], split=[0, G]`` is the baseline."""
+             arity: Sequence[int], split: Sequence[int], threads: int = 0, kraus=None) -> np.ndarray:
+    """Histogram (uint64[2^n]) of the tree Monte-Carlo; ``arity=[N], split=[0, G]`` is the baseline.
+    ``kraus``: the channel array of kraus_params (None: depolarizing and readout noise only)."""
     m = _Marshalled(circuit)
     a, s = _tree_arrays(arity, split)
+    k = _kr(kraus)
     counts = np.zeros(1 << m.n, dtype=np.uint64)
-    rc = lib().orc_run_tree(*m.args(), p1, p2, pm, shots, seed, len(a), _ptr(a, C.c_uint64),
-                            _ptr(s, C.c_int), threads, _ptr(counts, C.c_uint64))
+    rc = lib().orc_run_tree_k(*m.args(), p1, p2, pm, None if k is None else _ptr(k, C.c_double), shots, seed,
+                              len(a), _ptr(a, C.c_uint64), _ptr(s, C.c_int), threads, _ptr(counts, C.c_uint64))
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return counts
 
 
-def run_baseline(circuit, p1, p2, pm, shots, seed, threads: int = 0) -> np.ndarray:
-    return run_tree(circuit, p1, p2, pm, shots, seed, [shots], [0, len(circuit.gates)], threads)
+def run_baseline(circuit, p1, p2, pm, shots, seed, threads: int = 0, kraus=None) -> np.ndarray:
+    return run_tree(circuit, p1, p2, pm, shots, seed, [shots], [0, len(circuit.gates)], threads, kraus)
 
 
-def node_state(circuit, p1, p2, seed, arity, split, level: int, node: int) -> np.ndarray:
+def node_state(circuit, p1, p2, seed, arity, split, level: int, node: int, kraus=None) -> np.ndarray:
     m = _Marshalled(circuit)
     a, s = _tree_arrays(arity, split)
+    k = _kr(kraus)
     out = np.zeros(2 << m.n, dtype=np.float64)
-    rc = lib().orc_node_state(*m.args(), p1, p2, seed, len(a), _ptr(a, C.c_uint64), _ptr(s, C.c_int),
-                              level, node, _ptr(out, C.c_double))
+    rc = lib().orc_node_state_k(*m.args(), p1, p2, None if k is None else _ptr(k, C.c_double), seed, len(a),
+                                _ptr(a, C.c_uint64), _ptr(s, C.c_int), level, node, _ptr(out, C.c_double))
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return out[0::2] + 1j * out[1::2]
 
 
-def leaf_outcome(circuit, p1, p2, pm, seed, arity, split, leaf: int) -> int:
+def leaf_outcome(circuit, p1, p2, pm, seed, arity, split, leaf: int, kraus=None) -> int:
     m = _Marshalled(circuit)
     a, s = _tree_arrays(arity, split)
-    y = lib().orc_leaf_outcome(*m.args(), p1, p2, pm, seed, len(a), _ptr(a, C.c_uint64),
-                               _ptr(s, C.c_int), leaf)
+    k = _kr(kraus)
+    y = lib().orc_leaf_outcome_k(*m.args(), p1, p2, pm, None if k is None else _ptr(k, C.c_double), seed,
+                                 len(a), _ptr(a, C.c_uint64), _ptr(s, C.c_int), leaf)
     if y < 0:
         raise MemoryError("oracle allocation failed")
     return int(y)

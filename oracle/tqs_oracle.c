@@ -38,7 +38,7 @@ enum {
     G_CX, G_CZ, G_CP, G_SWAP, G_U1, G_U2
 };
 
-enum { DOM_NOISE = 1, DOM_MEAS = 2, DOM_READ = 3 };
+enum { DOM_NOISE = 1, DOM_MEAS = 2, DOM_READ = 3, DOM_KRAUS = 4 };
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10: ten rounds of the 4x32 S-box with a Weyl key schedule.      */
@@ -255,6 +255,95 @@ static void apply_noise(cplx *psi, const circuit *c, int g, uint64_t seed, uint6
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Non-unitary channels by quantum trajectories (Sec. 4.3: thermal relaxation, */
+/* amplitude damping and phase damping, each a set of Kraus operators).        */
+/* ------------------------------------------------------------------------- */
+/* Channel parameters, 6 doubles: kr[0] amplitude-damping gamma, kr[1]
+ * phase-damping lambda, kr[2..3] the (gamma, lambda) pair that thermal
+ * relaxation amounts to after a one-qubit gate, kr[4..5] the same after a
+ * two-qubit gate (see orc_thermal_params).  A zero entry is no channel.
+ *
+ * After a gate and its depolarizing Pauli, each qubit of the gate (q0, then q1)
+ * goes through, in this order: the thermal-relaxation damping, the
+ * thermal-relaxation dephasing, amplitude damping, phase damping.  Each is one
+ * trajectory step: with the normalised state psi and P1 = sum_{x_q = 1} |psi_x|^2,
+ * the "jump" Kraus operator K1 is chosen with probability r * P1 (r = gamma or
+ * lambda), else K0, and psi <- K psi / sqrt(probability of the choice):
+ *   amplitude damping  K0 = diag(1, sqrt(1-gamma)),  K1 = sqrt(gamma) |0><1|
+ *   phase damping      K0 = diag(1, sqrt(1-lambda)), K1 = sqrt(lambda) |1><1|
+ * (Nielsen & Chuang, Sec. 8.3.5-8.3.6).  The choice draws u in [0, 1) with 53
+ * bits from counter (node_lo, node_hi, 16 g + 8 i + c, 4), i = 0/1 the gate's
+ * qubit and c = 0..3 the channel in the order above; K1 iff u < r * P1. */
+static double kraus_u(uint64_t seed, uint64_t node, uint32_t index)
+{
+    uint32_t r[4];
+    draw(seed, node, index, DOM_KRAUS, r);
+    return ((double)(r[0] >> 5) * 67108864.0 + (double)(r[1] >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+static void kraus_step(cplx *psi, int n, int q, double rate, int damping, double u)
+{
+    uint64_t dim = (uint64_t)1 << n, bit = (uint64_t)1 << q;
+    double total = 0.0, one = 0.0;
+    for (uint64_t x = 0; x < dim; x++) {
+        double w = creal(psi[x]) * creal(psi[x]) + cimag(psi[x]) * cimag(psi[x]);
+        total += w;
+        if (x & bit)
+            one += w;
+    }
+    double pj = rate * one / total;
+    if (u < pj) {
+        double sc = sqrt(rate / (pj * total));
+        for (uint64_t x = 0; x < dim; x++) {
+            if (!(x & bit))
+                continue;
+            if (damping) { /* sqrt(gamma) |0><1| */
+                psi[x & ~bit] = sc * psi[x];
+                psi[x] = 0.0;
+            } else { /* sqrt(lambda) |1><1| */
+                psi[x & ~bit] = 0.0;
+                psi[x] = sc * psi[x];
+            }
+        }
+    } else {
+        double s0 = 1.0 / sqrt((1.0 - pj) * total), s1 = sqrt(1.0 - rate) * s0;
+        for (uint64_t x = 0; x < dim; x++)
+            psi[x] *= (x & bit) ? s1 : s0;
+    }
+}
+
+static void apply_kraus(cplx *psi, const circuit *c, int g, uint64_t seed, uint64_t node, const double *kr)
+{
+    if (!kr)
+        return;
+    int two = gate_arity(c->kind[g]) == 2;
+    double rate[4] = {kr[two ? 4 : 2], kr[two ? 5 : 3], kr[0], kr[1]};
+    int damping[4] = {1, 0, 1, 0};
+    for (int i = 0; i <= two; i++) {
+        int q = i ? c->q1[g] : c->q0[g];
+        for (int ch = 0; ch < 4; ch++)
+            if (rate[ch] > 0.0)
+                kraus_step(psi, c->n, q, rate[ch], damping[ch], kraus_u(seed, node, 16u * (uint32_t)g + 8u * (uint32_t)i + (uint32_t)ch));
+    }
+}
+
+/* The (gamma, lambda) of amplitude damping followed by phase damping that make
+ * up thermal relaxation towards |0> over a gate of duration t with times T1 and
+ * T2 <= 2 T1: gamma = 1 - exp(-t/T1) (population decay) and
+ * lambda = 1 - exp(t/T1 - 2t/T2), so that the coherence decays by
+ * sqrt(1-gamma) sqrt(1-lambda) = exp(-t/T2).  Returns -1 when T2 > 2 T1. */
+int orc_thermal_params(double t1, double t2, double t, double *gamma, double *lambda)
+{
+    if (t1 <= 0.0 || t2 <= 0.0 || t2 > 2.0 * t1 || t < 0.0)
+        return -1;
+    *gamma = 1.0 - exp(-t / t1);
+    *lambda = 1.0 - exp(t / t1 - 2.0 * t / t2);
+    if (*lambda < 0.0)
+        *lambda = 0.0;
+    return 0;
+}
+
 /* Measurement: the smallest y (in index order) whose running sum of |psi_y|^2
  * exceeds u * total; if rounding leaves none, the last y with nonzero weight. */
 static uint64_t sample_index(const cplx *psi, int n, double u)
@@ -336,6 +425,7 @@ typedef struct {
     double p1, p2, pm;
     uint64_t *counts;
     cplx **stack; /* one state per level */
+    const double *kr; /* channel parameters (apply_kraus) or NULL */
 } tree_run;
 
 static void run_node(tree_run *R, int level, uint64_t m)
@@ -352,6 +442,7 @@ static void run_node(tree_run *R, int level, uint64_t m)
     for (int g = R->t->split[level]; g < R->t->split[level + 1]; g++) {
         apply_gate(psi, c, g);
         apply_noise(psi, c, g, R->seed, m, R->p1, R->p2);
+        apply_kraus(psi, c, g, R->seed, m, R->kr);
     }
     if (level == R->t->L - 1) {
         uint64_t y = sample_index(psi, c->n, orc_measure_u(R->seed, m));
@@ -371,10 +462,25 @@ static void run_node(tree_run *R, int level, uint64_t m)
  * tree (N).  counts: 2^n uint64, zeroed here.  Level-0 subtrees are independent
  * and run on `threads` OpenMP threads (0 = default), each with its own
  * histogram; the summed histogram does not depend on the thread count. */
+int orc_run_tree_k(int n, int G, const int *kind, const int *q0, const int *q1,
+                   const double *theta, const double *mat, double p1, double p2, double pm,
+                   const double *kr, uint64_t N, uint64_t seed, int L, const uint64_t *arity,
+                   const int *split, int threads, uint64_t *counts);
+
 int orc_run_tree(int n, int G, const int *kind, const int *q0, const int *q1,
                  const double *theta, const double *mat, double p1, double p2, double pm,
                  uint64_t N, uint64_t seed, int L, const uint64_t *arity, const int *split,
                  int threads, uint64_t *counts)
+{
+    return orc_run_tree_k(n, G, kind, q0, q1, theta, mat, p1, p2, pm, NULL, N, seed, L, arity, split,
+                          threads, counts);
+}
+
+/* As orc_run_tree, with the non-unitary channels of `kr` (apply_kraus; NULL = none). */
+int orc_run_tree_k(int n, int G, const int *kind, const int *q0, const int *q1,
+                   const double *theta, const double *mat, double p1, double p2, double pm,
+                   const double *kr, uint64_t N, uint64_t seed, int L, const uint64_t *arity,
+                   const int *split, int threads, uint64_t *counts)
 {
     circuit c = {n, G, kind, q0, q1, theta, mat};
     tree t;
@@ -402,7 +508,7 @@ int orc_run_tree(int n, int G, const int *kind, const int *q0, const int *q1,
 #pragma omp atomic write
             fail = 1;
         } else {
-            tree_run R = {&c, &t, seed, p1, p2, pm, local, stack};
+            tree_run R = {&c, &t, seed, p1, p2, pm, local, stack, kr};
 #pragma omp for schedule(dynamic, 1)
             for (int64_t m = 0; m < (int64_t)roots; m++)
                 run_node(&R, 0, (uint64_t)m);
@@ -420,10 +526,25 @@ int orc_run_tree(int n, int G, const int *kind, const int *q0, const int *q1,
 
 /* State (logical, including Pauli noise and global phases) of node m at
  * `level` after its subcircuit, computed along its ancestor chain. */
+int orc_node_state_k(int n, int G, const int *kind, const int *q0, const int *q1,
+                     const double *theta, const double *mat, double p1, double p2, const double *kr,
+                     uint64_t seed, int L, const uint64_t *arity, const int *split, int level,
+                     uint64_t m, double *psi_out);
+
 int orc_node_state(int n, int G, const int *kind, const int *q0, const int *q1,
                    const double *theta, const double *mat, double p1, double p2, uint64_t seed,
                    int L, const uint64_t *arity, const int *split, int level, uint64_t m,
                    double *psi_out)
+{
+    return orc_node_state_k(n, G, kind, q0, q1, theta, mat, p1, p2, NULL, seed, L, arity, split, level, m,
+                            psi_out);
+}
+
+/* As orc_node_state, with the non-unitary channels of `kr` (NULL = none). */
+int orc_node_state_k(int n, int G, const int *kind, const int *q0, const int *q1,
+                     const double *theta, const double *mat, double p1, double p2, const double *kr,
+                     uint64_t seed, int L, const uint64_t *arity, const int *split, int level,
+                     uint64_t m, double *psi_out)
 {
     circuit c = {n, G, kind, q0, q1, theta, mat};
     (void)L;
@@ -440,6 +561,7 @@ int orc_node_state(int n, int G, const int *kind, const int *q0, const int *q1,
         for (int g = split[i]; g < split[i + 1]; g++) {
             apply_gate(psi, &c, g);
             apply_noise(psi, &c, g, seed, chain[i], p1, p2);
+            apply_kraus(psi, &c, g, seed, chain[i], kr);
         }
     memcpy(psi_out, psi, dim * sizeof(cplx));
     free(psi);
@@ -448,17 +570,31 @@ int orc_node_state(int n, int G, const int *kind, const int *q0, const int *q1,
 
 /* Outcome (after readout error) of a single leaf, computed along its chain.
  * Lets tests check arbitrary leaves of trees too large to run in full. */
+int64_t orc_leaf_outcome_k(int n, int G, const int *kind, const int *q0, const int *q1,
+                           const double *theta, const double *mat, double p1, double p2, double pm,
+                           const double *kr, uint64_t seed, int L, const uint64_t *arity,
+                           const int *split, uint64_t leaf);
+
 int64_t orc_leaf_outcome(int n, int G, const int *kind, const int *q0, const int *q1,
                          const double *theta, const double *mat, double p1, double p2, double pm,
                          uint64_t seed, int L, const uint64_t *arity, const int *split,
                          uint64_t leaf)
 {
+    return orc_leaf_outcome_k(n, G, kind, q0, q1, theta, mat, p1, p2, pm, NULL, seed, L, arity, split, leaf);
+}
+
+/* As orc_leaf_outcome, with the non-unitary channels of `kr` (NULL = none). */
+int64_t orc_leaf_outcome_k(int n, int G, const int *kind, const int *q0, const int *q1,
+                           const double *theta, const double *mat, double p1, double p2, double pm,
+                           const double *kr, uint64_t seed, int L, const uint64_t *arity,
+                           const int *split, uint64_t leaf)
+{
     uint64_t dim = (uint64_t)1 << n;
     double *psi = malloc(2 * dim * sizeof(double));
     if (!psi)
         return -1;
-    orc_node_state(n, G, kind, q0, q1, theta, mat, p1, p2, seed, L, arity, split, L - 1, leaf,
-                   psi);
+    orc_node_state_k(n, G, kind, q0, q1, theta, mat, p1, p2, kr, seed, L, arity, split, L - 1, leaf,
+                     psi);
     uint64_t y = sample_index((const cplx *)psi, n, orc_measure_u(seed, leaf));
     y ^= orc_readout_mask(seed, leaf, n, pm);
     free(psi);
