@@ -92,6 +92,29 @@ void tqs_circuit_destroy(tqs_circuit *c);
 tqs_status tqs_noise_model(double p1, double p2, double pm, tqs_noise **out);
 void tqs_noise_destroy(tqs_noise *nz);
 
+/* Noise model with the non-unitary channels of Sec. 4.3 as well.  After every
+ * gate and its depolarizing Pauli, each of the gate's qubits (q0, then q1) goes
+ * through, in this order: thermal relaxation (when t1 > 0: amplitude damping
+ * with gamma = 1 - exp(-t/T1) then phase damping with
+ * lambda = 1 - exp(t/T1 - 2t/T2), t = time_1q or time_2q by the gate's arity;
+ * needs 0 < T2 <= 2 T1), amplitude damping with ad_gamma, phase damping with
+ * pd_lambda.  Each channel is one quantum-trajectory step: with P1 the
+ * probability of the qubit being 1 in the normalised state, the jump operator
+ * (amplitude damping sqrt(gamma)|0><1|, phase damping sqrt(lambda)|1><1|) is
+ * chosen with probability rate * P1, else diag(1, sqrt(1 - rate)), and the
+ * state is renormalised; the choice compares u = ((w0>>5)*2^26 + (w1>>6)) * 2^-53
+ * of Philox4x32-10 counter (node_lo, node_hi, 16 g + 8 i + c, 4) with rate * P1
+ * (g the gate, i = 0/1 its qubit, c = 0..3 the channel in the order above).
+ * Rates and probabilities in [0, 1], times >= 0, else EINVAL.  A zero rate
+ * (t1 = 0) means no such channel.  Every gate with a channel ends a tile pass:
+ * the channel's choice needs a reduction over the whole state. */
+typedef struct {
+    double p1, p2, pm;
+    double ad_gamma, pd_lambda;
+    double t1, t2, time_1q, time_2q;
+} tqs_noise_params;
+tqs_status tqs_noise_model_ex(const tqs_noise_params *params, tqs_noise **out);
+
 typedef enum { TQS_MODE_BASELINE = 0, TQS_MODE_TREE = 1 } tqs_mode;
 typedef enum { TQS_FP64 = 0, TQS_FP32 = 1 } tqs_precision;
 typedef enum {

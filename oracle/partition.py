@@ -147,6 +147,20 @@ def xcp(shots: int, levels: int, G: int, ratio: int = 2) -> Tuple[List[int], Lis
         a += 1
 
 
-def gate_rates(circuit, p1: float, p2: float) -> List[float]:
+def gate_rates(circuit, p1: float, p2: float, kraus=None) -> List[float]:
+    """Per-gate error rate e_i for DCP: the depolarizing probability and, with
+    damping channels (the oracle's channel array, core.kraus_params), the
+    probability that any of them jumps, bounded by its rate on each of the
+    gate's qubits."""
     two = {"cx", "cz", "cp", "swap", "u2"}
-    return [p2 if g[0] in two else p1 for g in circuit.gates]
+    out = []
+    for g in circuit.gates:
+        t = g[0] in two
+        keep = 1.0 - (p2 if t else p1)
+        if kraus is not None:
+            rates = [kraus[4] if t else kraus[2], kraus[5] if t else kraus[3], kraus[0], kraus[1]]
+            for _ in range(2 if t else 1):
+                for r in rates:
+                    keep *= 1.0 - r
+        out.append(1.0 - keep)
+    return out

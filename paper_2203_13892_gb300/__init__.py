@@ -18,6 +18,7 @@ from .capi import (  # noqa: F401
     options,
     tqs_abi_version,
     tqs_circuit_create,
+    tqs_noise_model_ex,
     tqs_circuit_destroy,
     tqs_debug_node_noise,
     tqs_debug_plan_order,

@@ -51,6 +51,12 @@ class tqs_gate(C.Structure):
                 ("theta", C.c_double), ("mat", C.POINTER(C.c_double))]
 
 
+class tqs_noise_params(C.Structure):
+    _fields_ = [("p1", C.c_double), ("p2", C.c_double), ("pm", C.c_double), ("ad_gamma", C.c_double),
+                ("pd_lambda", C.c_double), ("t1", C.c_double), ("t2", C.c_double), ("time_1q", C.c_double),
+                ("time_2q", C.c_double)]
+
+
 class tqs_options(C.Structure):
     _fields_ = [("mode", C.c_int), ("prec", C.c_int), ("part", C.c_int),
                 ("z", C.c_double), ("eps", C.c_double), ("copy_gates", C.c_uint32),
@@ -89,7 +95,7 @@ _lib = None
 
 # Exported symbols, by header declaration.
 EXPORTS = (
-    "tqs_circuit_create", "tqs_circuit_destroy", "tqs_noise_model", "tqs_noise_destroy",
+    "tqs_circuit_create", "tqs_circuit_destroy", "tqs_noise_model", "tqs_noise_model_ex", "tqs_noise_destroy",
     "tqs_options_default", "tqs_partition", "tqs_simulate", "tqs_plan_create",
     "tqs_plan_execute", "tqs_plan_workspace_bytes", "tqs_plan_host_pool_bytes", "tqs_plan_destroy",
     "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_debug_plan_order", "tqs_simulate_static",
@@ -120,6 +126,8 @@ def lib():
             L.tqs_circuit_destroy.argtypes = [vp]
             L.tqs_noise_model.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(vp)]
             L.tqs_noise_model.restype = st
+            L.tqs_noise_model_ex.argtypes = [C.POINTER(tqs_noise_params), C.POINTER(vp)]
+            L.tqs_noise_model_ex.restype = st
             L.tqs_noise_destroy.argtypes = [vp]
             L.tqs_options_default.argtypes = [C.POINTER(tqs_options)]
             L.tqs_partition.argtypes = [vp, vp, C.c_uint64, C.POINTER(tqs_options), u32p, u64p, u32p]
@@ -247,6 +255,15 @@ def circuit(c) -> Handle:
 
 def tqs_circuit_destroy(h: Handle) -> None:
     h.close()
+
+
+def tqs_noise_model_ex(p1: float, p2: float, pm: float, ad_gamma: float = 0.0, pd_lambda: float = 0.0,
+                       t1: float = 0.0, t2: float = 0.0, time_1q: float = 0.0, time_2q: float = 0.0) -> Handle:
+    prm = tqs_noise_params(float(p1), float(p2), float(pm), float(ad_gamma), float(pd_lambda), float(t1),
+                           float(t2), float(time_1q), float(time_2q))
+    out = C.c_void_p()
+    _check(lib().tqs_noise_model_ex(C.byref(prm), C.byref(out)))
+    return Handle(out, lib().tqs_noise_destroy)
 
 
 def tqs_noise_model(p1: float, p2: float, pm: float) -> Handle:

@@ -198,7 +198,47 @@ tqs_status tqs_noise_model(double p1, double p2, double pm, tqs_noise **out)
     tqs_noise *n = new (std::nothrow) tqs_noise();
     if (!n)
         return fail(TQS_ENOMEM, "host allocation failed");
-    n->nz = {p1, p2, pm};
+    n->nz.p1 = p1;
+    n->nz.p2 = p2;
+    n->nz.pm = pm;
+    *out = n;
+    return TQS_OK;
+}
+
+tqs_status tqs_noise_model_ex(const tqs_noise_params *q, tqs_noise **out)
+{
+    if (!out || !q)
+        return fail(TQS_EINVAL, "params and out are required");
+    for (double p : {q->p1, q->p2, q->pm, q->ad_gamma, q->pd_lambda})
+        if (!(p >= 0.0 && p <= 1.0))
+            return fail(TQS_EINVAL, "probabilities and damping rates must lie in [0, 1]");
+    for (double t : {q->t1, q->t2, q->time_1q, q->time_2q})
+        if (!(t >= 0.0) || !std::isfinite(t))
+            return fail(TQS_EINVAL, "times must be finite and >= 0");
+    tqs::Noise nz;
+    nz.p1 = q->p1;
+    nz.p2 = q->p2;
+    nz.pm = q->pm;
+    nz.ad = q->ad_gamma;
+    nz.pd = q->pd_lambda;
+    if (q->t1 > 0.0) {
+        if (!(q->t2 > 0.0 && q->t2 <= 2.0 * q->t1))
+            return fail(TQS_EINVAL, "thermal relaxation needs 0 < T2 <= 2 T1");
+        // population decay exp(-t/T1) and coherence decay exp(-t/T2) as amplitude
+        // damping followed by phase damping
+        auto pair = [&](double t, double &g, double &l) {
+            g = 1.0 - std::exp(-t / q->t1);
+            l = 1.0 - std::exp(t / q->t1 - 2.0 * t / q->t2);
+            if (l < 0.0)
+                l = 0.0;
+        };
+        pair(q->time_1q, nz.tr_g1, nz.tr_l1);
+        pair(q->time_2q, nz.tr_g2, nz.tr_l2);
+    }
+    tqs_noise *n = new (std::nothrow) tqs_noise();
+    if (!n)
+        return fail(TQS_ENOMEM, "host allocation failed");
+    n->nz = nz;
     *out = n;
     return TQS_OK;
 }

@@ -149,6 +149,10 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
         o_meta[i] = take(sizeof(NodeMeta) * (np + 1) * B);
     }
     size_t o_S = take(sizeof(double) * H.samp.groups * B);
+    // every pass of a plan has the same tile width, min(n, tile_max)
+    const uint64_t tiles = (uint64_t)1 << (H.n - std::min<uint32_t>(H.n, H.tile_max));
+    size_t o_ksum = take(H.kraus ? sizeof(double) * 4 * tiles * B : 0);
+    size_t o_kmat = take(H.kraus ? esz * 8 * B : 0);
     if (assign) {
         char *b = (char *)ws;
         d_instr = (Instr *)(b + o_instr);
@@ -176,6 +180,8 @@ size_t DevicePlan::layout(uint64_t B, bool assign)
             meta[i] = (NodeMeta *)(b + o_meta[i]);
         }
         d_S = (double *)(b + o_S);
+        d_ksum = H.kraus ? (double *)(b + o_ksum) : nullptr;
+        d_kmat = H.kraus ? (void *)(b + o_kmat) : nullptr;
     }
     return off;
 }
@@ -310,6 +316,35 @@ void DevicePlan::set_debug(PassLaunch &a) const
         a.out_slots = batch - 1;  // understated on purpose: the kernels' own check must catch it
 }
 
+void DevicePlan::set_kraus(PassLaunch &a, const Pass &ps) const
+{
+    a.kmat = d_kmat;
+    a.ksum = ps.kout_gate >= 0 ? d_ksum : nullptr;
+    a.knq = ps.kout_nq;
+    a.kp0 = ps.kout_p0;
+    a.kp1 = ps.kout_p1;
+}
+
+int DevicePlan::launch_choice(const Pass &ps, uint64_t lo, uint64_t nn, uint64_t seed, const uint64_t *sdev)
+{
+    const PlanHost &H = host;
+    KrausLaunch k;
+    std::memset(&k, 0, sizeof(k));
+    k.ksum = d_ksum;
+    k.tiles = (uint64_t)1 << (H.n - ps.t);
+    k.kmat = d_kmat;
+    k.fp64 = H.prec == TQS_FP64;
+    k.node_lo = lo;
+    k.nnodes = nn;
+    k.seed_dev = sdev;
+    k.seed = seed;
+    k.gate = (uint32_t)ps.kout_gate;
+    k.nq = ps.kout_nq;
+    for (int c = 0; c < 4; c++)
+        k.rate[c] = H.krate[ps.kout_nq == 2 ? 1 : 0][c];
+    return launch_kraus(k, stream);
+}
+
 tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vector<uint64_t> &plo,
                                  uint64_t seed, unsigned long long *counts, std::string &err)
 {
@@ -384,6 +419,7 @@ tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vect
         a.thrm = H.thrm;
         // state bytes a pass must move: read its input (nothing when it starts
         // from |0...0>) and, unless it only measures, write its output
+        set_kraus(a, ps);
         const double rd = a.in ? sb : 0.0;
         if (leaf && pl + 1 == np) {
             const double sums = 8.0 * (double)H.samp.groups;
@@ -397,6 +433,8 @@ tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vect
             a.mode = MODE_STORE;
             CKP(TQS_PROF_STORE, (double)nn * (rd + sb), launch_pass(a, stream));
             alg_bytes += (double)nn * (rd + sb);
+            if (ps.kout_gate >= 0)
+                CKP(TQS_PROF_NOISE, (double)nn * 64.0, launch_choice(ps, lo, nn, seed, seed_dev));
         }
     }
     if (i + 1 < L) {
@@ -508,7 +546,10 @@ tqs_status DevicePlan::run_chain(uint32_t level, uint64_t node, uint64_t seed, s
             a.meta_stride = np + 1;
             a.pass_local = pl;
             a.seed = seed;
+            set_kraus(a, ps);
             CKL(launch_pass(a, stream));
+            if (ps.kout_gate >= 0)
+                CKL(launch_choice(ps, chain[i], 1, seed, nullptr));
         }
     }
     return TQS_OK;

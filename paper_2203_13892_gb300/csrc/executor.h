@@ -35,6 +35,8 @@ struct DevicePlan {
     uint8_t *d_perm = nullptr;
     unsigned long long *d_counts_internal = nullptr;
     double *d_S = nullptr;
+    double *d_ksum = nullptr;   // damping channels: per-tile sums of the last boundary pass
+    void *d_kmat = nullptr;     // damping channels: each node's chosen operators
     // Levels whose state slots live in pinned host memory mapped into the
     // device's address space (bit i = level i): the pass kernels read and write
     // them in place (on a Grace-Blackwell node over NVLink-C2C), so the state pool
@@ -74,6 +76,9 @@ struct DevicePlan {
     // reads and clears the device error word (synchronises the stream)
     tqs_status check_device_error(std::string &err);
     void set_debug(PassLaunch &a) const;
+    // damping channels: the boundary sums of pass `ps` and, after it, the choice launch
+    void set_kraus(PassLaunch &a, const Pass &ps) const;
+    int launch_choice(const Pass &ps, uint64_t lo, uint64_t nn, uint64_t seed, const uint64_t *seed_dev);
     bool profiling() const { return (opts.flags & TQS_FLAG_PROFILE) != 0; }
 };
 

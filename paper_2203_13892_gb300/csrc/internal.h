@@ -16,7 +16,7 @@ constexpr int kMaxTile = 13;       // largest shared-memory tile (2^13 amplitude
 constexpr int kMaxGamma = 8;       // sampler group = up to 2^8 consecutive outcomes
 constexpr int kProgChunkBytes = 6144;  // pass-program bytes staged in shared memory at a time
 constexpr int kNoiseStage = 4096;      // noise bytes of a node staged in shared memory
-constexpr uint32_t kDomNoise = 1, kDomMeas = 2, kDomRead = 3;
+constexpr uint32_t kDomNoise = 1, kDomMeas = 2, kDomRead = 3, kDomKraus = 4;
 
 // ---------------------------------------------------------------------------
 // Device-visible plan records
@@ -61,6 +61,12 @@ struct Circuit {
 
 struct Noise {
     double p1, p2, pm;
+    // non-unitary channels per qubit of a gate, in the order applied: thermal
+    // relaxation's damping and dephasing (by the gate's arity), amplitude
+    // damping, phase damping (rates; 0 = none)
+    double ad = 0.0, pd = 0.0;
+    double tr_g1 = 0.0, tr_l1 = 0.0, tr_g2 = 0.0, tr_l2 = 0.0;
+    bool kraus() const { return ad > 0.0 || pd > 0.0 || tr_g1 > 0.0 || tr_l1 > 0.0 || tr_g2 > 0.0 || tr_l2 > 0.0; }
 };
 
 // Compiled pass program: 16-byte aligned records walked in order by every
@@ -88,7 +94,10 @@ struct Noise {
 //               The kernels apply it as one 2^k x 2^k complex product on the tensor cores
 //               (FP32 states only, k = t - 7 so that a tile has 128 columns).
 //   REC_END     no payload: the end of the pass's program (every pass has one)
-enum RecType : uint8_t { REC_DENSE1 = 1, REC_DENSE2 = 2, REC_RUN = 3, REC_FUSED = 4, REC_END = 5 };
+//   REC_KRAUS   a=j0 b=j1 c=p0 d=p1 e=qubits (1 or 2), no payload: the damping operators
+//               chosen for this node after the previous gate, read per node from the
+//               plan's operator buffer (2x2 on p0, then 2x2 on p1)
+enum RecType : uint8_t { REC_DENSE1 = 1, REC_DENSE2 = 2, REC_RUN = 3, REC_FUSED = 4, REC_END = 5, REC_KRAUS = 6 };
 enum FacKind : uint8_t {
     FAC_A_FIXED = 1,   // a^{x_p}, p a thread bit or outside the tile
     FAC_A_SLOT = 2,    // a^{x}, on slot bit s = j0 - 8
@@ -147,6 +156,13 @@ struct Pass {
     uint32_t t, L;                // tile width and number of contiguous low bits
     uint8_t tbits[kMaxTile];      // physical bit of each tile position (ascending)
     uint8_t hbits[32];            // remaining physical bits (ascending), n - t of them
+    // Damping channels (a plan with Noise::kraus(): one gate per pass).  The
+    // pass's epilogue writes the sums the choice after gate kout_gate needs
+    // (kout_gate < 0: none); the REC_KRAUS record that opens the next pass
+    // applies the chosen operators on kin_p0 (and kin_p1).
+    int32_t kout_gate = -1;
+    uint8_t kout_nq = 0, kout_p0 = 0, kout_p1 = 0;
+    uint8_t kin_nq = 0, kin_p0 = 0, kin_p1 = 0;
 };
 
 struct Level {
@@ -189,6 +205,11 @@ struct PlanHost {
     uint64_t thr1, thr2, thrm;     // floor(p * 2^32)
     SamplerLayout samp;
     uint32_t tile_max;
+    // damping channels: rates after a one-qubit (krate[0]) and a two-qubit gate
+    // (krate[1]), per qubit in the order applied: thermal damping, thermal
+    // dephasing, amplitude damping, phase damping
+    bool kraus = false;
+    double krate[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
 };
 
 // Host planning (planner.cpp)
@@ -267,9 +288,31 @@ struct PassLaunch {
                                // 4 = an index check failed), [1] check code, [2] offending value
     uint32_t dbg;              // kDbgBounds | kDbgFaultTimeout
     uint64_t in_slots, out_slots;  // state slots of the input and output buffers (index checks)
+    // damping channels: the epilogue writes, per tile, the four sums of |a|^2 by
+    // the logical values of bits kp0 (low) and kp1 to ksum[slot][tile][4] (FP64;
+    // nullptr = no sums); REC_KRAUS records read the node's operators from kmat
+    double *ksum;
+    const void *kmat;          // [slot][8] complex in the state's precision (2x2 on p0, 2x2 on p1)
+    uint32_t knq, kp0, kp1;
 };
 constexpr uint32_t kDbgBounds = 1u, kDbgFaultTimeout = 2u;
 int launch_pass(const PassLaunch &a, void *stream);
+
+// The damping choices after one gate for `nnodes` nodes: sums the per-tile
+// |a|^2 sums in a fixed order, draws and decides each channel in turn (the
+// trajectory step of Sec. 4.3) and writes each node's 2x2 operators.
+struct KrausLaunch {
+    const double *ksum;        // [slot][tiles][4]
+    uint64_t tiles;
+    void *kmat;                // [slot][8] complex (state precision)
+    int fp64;
+    uint64_t node_lo, nnodes;
+    const uint64_t *seed_dev;  // when non-null the seed is read here (graph replays)
+    uint64_t seed;
+    uint32_t gate, nq;
+    double rate[4];            // thermal damping, thermal dephasing, amplitude damping, phase damping
+};
+int launch_kraus(const KrausLaunch &a, void *stream);
 // Sets the shared-memory limits of every kernel variant (call before a stream capture).
 int prepare_kernels();
 

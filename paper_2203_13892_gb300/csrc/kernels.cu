@@ -142,6 +142,11 @@ int launch_pass(const PassLaunch &a, void *stream)
     k.fused_k = a.fused ? a.fused_k : 0;
     k.err = a.err;
     k.dbg = a.dbg;
+    k.ksum = a.ksum;
+    k.kmat = a.kmat;
+    k.knq = a.knq;
+    k.kp0 = a.kp0;
+    k.kp1 = a.kp1;
     k.in_slots = a.in_slots;
     k.out_slots = a.out_slots;
     k.thrm = a.thrm;
@@ -184,6 +189,113 @@ int launch_pass(const PassLaunch &a, void *stream)
     return launch_pass_r<float, MODE_SAMPLE>(k, logr, grid, smem, st);
 }
 
+
+// ---------------------------------------------------------------------------
+// Damping channels: the trajectory choice after one gate (Sec. 4.3)
+// ---------------------------------------------------------------------------
+// One warp per node.  The lanes add the per-tile sums in a fixed order (lane
+// l takes tiles l, l+32, ...; then a fixed butterfly), so the result does not
+// depend on scheduling.  Lane 0 then goes through the channels of the gate's
+// qubits in order: with P the normalised joint distribution of the (one or
+// two) qubits' logical values, a channel of rate r on qubit i jumps iff
+// u < r * P(bit i = 1), u drawn from counter (node_lo, node_hi, 16 g + 8 i + c,
+// 4); the jump operator is sqrt(r)|0><1| (damping) or sqrt(r)|1><1|
+// (dephasing), otherwise diag(1, sqrt(1-r)), each divided by the square root
+// of the probability of the choice, and P follows the choice.  The operators
+// of each qubit are multiplied up (the first also carries 1/sqrt(total), which
+// renormalises the state as it stands) and stored for the next pass.
+__global__ void __launch_bounds__(256) kraus_kernel(const __grid_constant__ KrausLaunch a)
+{
+    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= a.nnodes)
+        return;
+    const double *S = a.ksum + w * a.tiles * 4;
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (uint64_t t = lane; t < a.tiles; t += 32)
+        for (int j = 0; j < 4; j++)
+            s4[j] += S[t * 4 + j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        for (int j = 0; j < 4; j++)
+            s4[j] += __shfl_xor_sync(0xffffffffu, s4[j], off);
+    if (lane != 0)
+        return;
+    const uint64_t node = a.node_lo + w;
+    const uint64_t seed = a.seed_dev ? *a.seed_dev : a.seed;
+    const double total = s4[0] + s4[1] + s4[2] + s4[3];
+    double P[4];
+    for (int j = 0; j < 4; j++)
+        P[j] = total > 0.0 ? s4[j] / total : 0.0;
+    // M[q] = [[m00, m01], [m10, m11]] as doubles (the operators are real)
+    double M[2][4] = {{1.0, 0.0, 0.0, 1.0}, {1.0, 0.0, 0.0, 1.0}};
+    double scale = total > 0.0 ? 1.0 / sqrt(total) : 1.0;
+    for (uint32_t i = 0; i < a.nq; i++) {
+        const uint32_t bit = 1u << i;
+        for (uint32_t c = 0; c < 4; c++) {
+            const double r = a.rate[c];
+            if (!(r > 0.0))
+                continue;
+            const bool damping = (c & 1u) == 0u;  // thermal damping, amplitude damping
+            double P1 = 0.0;
+            for (uint32_t x = 0; x < 4; x++)
+                if (x & bit)
+                    P1 += P[x];
+            const double pj = r * P1;
+            const uint4 rr = draw(seed, node, 16u * a.gate + 8u * i + c, kDomKraus);
+            const double u = ((double)(rr.x >> 5) * 67108864.0 + (double)(rr.y >> 6)) * (1.0 / 9007199254740992.0);
+            double K[4];
+            double Pn[4] = {0.0, 0.0, 0.0, 0.0};
+            if (u < pj) {
+                const double sc = sqrt(r / pj);
+                if (damping) {
+                    K[0] = 0.0; K[1] = sc; K[2] = 0.0; K[3] = 0.0;
+                    for (uint32_t x = 0; x < 4; x++)
+                        if (x & bit)
+                            Pn[x ^ bit] = P[x] * r / pj;
+                } else {
+                    K[0] = 0.0; K[1] = 0.0; K[2] = 0.0; K[3] = sc;
+                    for (uint32_t x = 0; x < 4; x++)
+                        if (x & bit)
+                            Pn[x] = P[x] * r / pj;
+                }
+            } else {
+                const double s0 = 1.0 / sqrt(1.0 - pj);
+                K[0] = s0; K[1] = 0.0; K[2] = 0.0; K[3] = sqrt(1.0 - r) * s0;
+                for (uint32_t x = 0; x < 4; x++)
+                    Pn[x] = P[x] * ((x & bit) ? (1.0 - r) : 1.0) / (1.0 - pj);
+            }
+            for (int x = 0; x < 4; x++)
+                P[x] = Pn[x];
+            double *m = M[i];
+            const double n00 = K[0] * m[0] + K[1] * m[2], n01 = K[0] * m[1] + K[1] * m[3];
+            const double n10 = K[2] * m[0] + K[3] * m[2], n11 = K[2] * m[1] + K[3] * m[3];
+            m[0] = n00; m[1] = n01; m[2] = n10; m[3] = n11;
+        }
+    }
+    for (int j = 0; j < 4; j++)
+        M[0][j] *= scale;
+    if (a.fp64) {
+        double2 *out = reinterpret_cast<double2 *>(a.kmat) + w * 8;
+        for (int q = 0; q < 2; q++)
+            for (int j = 0; j < 4; j++)
+                out[q * 4 + j] = make_double2(M[q][j], 0.0);
+    } else {
+        float2 *out = reinterpret_cast<float2 *>(a.kmat) + w * 8;
+        for (int q = 0; q < 2; q++)
+            for (int j = 0; j < 4; j++)
+                out[q * 4 + j] = make_float2((float)M[q][j], 0.0f);
+    }
+}
+
+int launch_kraus(const KrausLaunch &a, void *stream)
+{
+    if (a.nnodes == 0)
+        return 0;
+    const uint64_t threads = a.nnodes * 32;
+    kraus_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 // Utility kernels

@@ -1240,6 +1240,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                     if (pz)
                         apply_noise(pz, 15, ha, hc, hb, hd);
                     p += 16u + 16u * CS;
+                } else if (htype == REC_KRAUS) {
+                    // this node's damping operators after the previous gate (real 2x2)
+                    const C *km = reinterpret_cast<const C *>(a.kmat) + (uint64_t)slot * 8;
+                    dense1_real(ha, hc, km[0].x, km[1].x, km[2].x, km[3].x);
+                    if (he == 2)
+                        dense1_real(hb, hd, km[4].x, km[5].x, km[6].x, km[7].x);
+                    p += 16u;
                 } else if (htype == REC_FUSED) {
                   if constexpr (!FUSE) {  // the host launches the FUSE instantiation for these
                     if (tid == 0 && a.err)
@@ -1444,6 +1451,39 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
     }
 
     // ---- epilogue ------------------------------------------------------
+    if (MODE == MODE_STORE && a.ksum) {
+        // damping channels: this tile's |a|^2 summed by the logical values of
+        // the next choice's qubits (bit kp0 -> index bit 0, kp1 -> bit 1)
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        if (active) {
+            const uint32_t tb0 = base | tphys;
+#pragma unroll
+            for (int k = 0; k < NR; k++) {
+                const uint32_t lg = (tb0 | soff[k]) ^ mask;
+                const uint32_t ix = ((lg >> a.kp0) & 1u) | (a.knq == 2 ? ((lg >> a.kp1) & 1u) << 1 : 0u);
+                const double w = (double)norm2<R>(v[k]);
+                s4[0] += ix == 0 ? w : 0.0;
+                s4[1] += ix == 1 ? w : 0.0;
+                s4[2] += ix == 2 ? w : 0.0;
+                s4[3] += ix == 3 ? w : 0.0;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            for (int j = 0; j < 4; j++)
+                s4[j] += __shfl_xor_sync(0xffffffffu, s4[j], off);
+        __syncthreads();
+        if ((tid & 31u) == 0)
+            for (int j = 0; j < 4; j++)
+                red[(tid >> 5) * 4 + j] = s4[j];
+        __syncthreads();
+        if (tid < 4) {
+            double t = 0.0;
+            for (int wi = 0; wi < kThreads / 32; wi++)
+                t += red[wi * 4 + tid];
+            a.ksum[((uint64_t)slot * gridDim.x + blockIdx.x) * 4 + tid] = t;
+        }
+    }
     if (MODE == MODE_STORE) {
         C *dst = reinterpret_cast<C *>(a.out) + (uint64_t)slot * a.state_elems;
         if (active) {

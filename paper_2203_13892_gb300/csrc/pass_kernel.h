@@ -27,6 +27,9 @@ struct PassK {
     unsigned int *err;
     uint64_t seed, thrm;
     uint64_t in_slots, out_slots;
+    double *ksum;
+    const void *kmat;
+    uint32_t knq, kp0, kp1;
     uint32_t dbg;
     uint32_t fused_k;
     uint32_t ibeg, iend, n, t, L, sites, meta_stride, pass_local;

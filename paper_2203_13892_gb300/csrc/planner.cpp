@@ -133,13 +133,28 @@ static bool pow_times_le(uint64_t a, uint32_t k, uint64_t b, uint64_t N)
 // and no larger than the state-copy limit (at least c gates per subcircuit,
 // Sec. 3.6); A_0 is then raised to ceil(N / A_r^k) so that the tree has N
 // leaves, and the circuit is cut into k+1 subcircuits of equal length.
+// Error rate e_i of gate i for DCP's first-subcircuit estimate (Sec. 3.2,
+// Eq. error_rate): its depolarizing probability and, with damping channels, the
+// probability that any of them jumps, bounded by its rate on each of the gate's
+// qubits (a jump's probability is rate * P1 <= rate).
+double gate_error_rate(const Noise &nz, uint32_t kind)
+{
+    const bool two = is_two_qubit(kind);
+    double keep = 1.0 - (two ? nz.p2 : nz.p1);
+    const double rates[4] = {two ? nz.tr_g2 : nz.tr_g1, two ? nz.tr_l2 : nz.tr_l1, nz.ad, nz.pd};
+    for (int q = 0; q < (two ? 2 : 1); q++)
+        for (double r : rates)
+            keep *= 1.0 - r;
+    return 1.0 - keep;
+}
+
 static std::string dcp(const Circuit &c, const Noise &nz, uint64_t N, double z, double eps,
                        uint32_t cgates, std::vector<uint64_t> &arity, std::vector<uint32_t> &split)
 {
     const uint32_t G = (uint32_t)c.gates.size();
     std::vector<double> e(G);
     for (uint32_t i = 0; i < G; i++)
-        e[i] = is_two_qubit(c.gates[i].kind) ? nz.p2 : nz.p1;
+        e[i] = gate_error_rate(nz, c.gates[i].kind);
     uint32_t cap = (cgates ? G / cgates : G);
     cap = cap >= 1 ? cap - 1 : 0;
     uint32_t K = cap;
@@ -188,7 +203,7 @@ uint64_t dcp_first_arity(const Circuit &c, const Noise &nz, uint64_t N, double z
     uint32_t first = G ? (G + K) / (K + 1) : 0;
     double prod = 1.0;
     for (uint32_t i = 0; i < first; i++)
-        prod *= (1.0 - (is_two_qubit(c.gates[i].kind) ? nz.p2 : nz.p1));
+        prod *= (1.0 - gate_error_rate(nz, c.gates[i].kind));
     double ph = 1.0 - prod;
     double n0 = z * z * ph * (1.0 - ph) / (eps * eps);
     double a = std::ceil(n0 / (1.0 + n0 / (double)N));
@@ -526,6 +541,18 @@ static void compile_programs(PlanHost &P)
         ps.fused_blocks = 0;
         P.chunk_off.push_back((uint32_t)out.size());
         chunk_start = out.size();
+        if (ps.kin_nq) {  // the damping operators chosen after the previous gate
+            RecHdr h;
+            std::memset(&h, 0, sizeof(h));
+            h.type = REC_KRAUS;
+            h.a = pos[ps.kin_p0];
+            h.b = ps.kin_nq == 2 ? pos[ps.kin_p1] : 0xff;
+            h.c = ps.kin_p0;
+            h.d = ps.kin_p1;
+            h.e = ps.kin_nq;
+            h.ibeg = h.iend = ps.ibeg;
+            put(&h, 16);
+        }
         // tensor-core fusion: FP32 states and tiles with 128 columns beside k = t - 7 fused qubits
         const uint32_t kf = (P.fuse && !f64 && (ps.t == 11 || ps.t == 12)) ? ps.t - 7 : 0;
         uint32_t k = ps.ibeg;
@@ -938,16 +965,38 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
             q |= (1u << low[g].p0) | (two ? (1u << low[g].p1) : 0u);
         return q;
     };
+    // With damping channels (Sec. 4.3) every gate's channel choice needs a
+    // reduction over the whole state after it, so every gate ends a pass and
+    // gates keep circuit order: pass k of a level holds gate g0+k, opened by the
+    // operators chosen after the previous gate of the level; one more pass,
+    // holding only those of the level's last gate, closes the level.
+    P.kraus = nz.kraus();
+    P.krate[0][0] = nz.tr_g1; P.krate[0][1] = nz.tr_l1; P.krate[0][2] = nz.ad; P.krate[0][3] = nz.pd;
+    P.krate[1][0] = nz.tr_g2; P.krate[1][1] = nz.tr_l2; P.krate[1][2] = nz.ad; P.krate[1][3] = nz.pd;
     for (uint32_t i = 0; i < L; i++) {
         Level &lv = P.levels[i];
         lv.pass_begin = (uint32_t)P.passes.size();
         std::vector<uint32_t> rem;
         for (uint32_t g = lv.g0; g < lv.g1; g++)
             rem.push_back(g);
+        uint8_t kin_nq = 0, kin_p0 = 0, kin_p1 = 0;
         do {
             uint32_t need = 0, blocked = 0;
             const uint32_t lowbits = (1u << std::min<uint32_t>(n, 4)) - 1;
             std::vector<uint32_t> take, left;
+            if (P.kraus) {
+                need = kin_nq ? ((1u << kin_p0) | (kin_nq == 2 ? (1u << kin_p1) : 0u)) : 0u;
+                if (!rem.empty()) {
+                    const uint32_t g = rem[0];
+                    if (op[g] == OP_DENSE1)
+                        need |= 1u << low[g].p0;
+                    else if (op[g] == OP_DENSE2)
+                        need |= (1u << low[g].p0) | (1u << low[g].p1);
+                    take.push_back(g);
+                    left.assign(rem.begin() + 1, rem.end());
+                }
+                rem.clear();
+            }
             for (uint32_t g : rem) {
                 const uint32_t q = gate_qubits(g);
                 uint32_t add = 0;
@@ -967,8 +1016,26 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
                 return "internal: pass scheduling made no progress";  // an empty level gets one empty pass
             Pass ps;
             std::memset(&ps, 0, sizeof(ps));
+            ps.kout_gate = -1;
             ps.level = i;
             ps.site_begin = take.empty() ? 0u : take[0] - lv.g0;
+            if (P.kraus) {
+                ps.kin_nq = kin_nq;
+                ps.kin_p0 = kin_p0;
+                ps.kin_p1 = kin_p1;
+                kin_nq = 0;
+                if (!take.empty()) {
+                    const uint32_t g = take[0];
+                    const bool two = is_two_qubit(c.gates[g].kind);
+                    ps.kout_gate = (int32_t)g;
+                    ps.kout_nq = two ? 2 : 1;
+                    ps.kout_p0 = low[g].np0;
+                    ps.kout_p1 = two ? low[g].np1 : low[g].np0;
+                    kin_nq = ps.kout_nq;
+                    kin_p0 = ps.kout_p0;
+                    kin_p1 = ps.kout_p1;
+                }
+            }
             choose_tile(n, tmax, need, nullptr, 0, ps);
             ps.ibeg = (uint32_t)P.instrs.size();
             uint8_t pos[32];
@@ -994,7 +1061,7 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
             ps.iend = (uint32_t)P.instrs.size();
             P.passes.push_back(ps);
             rem.swap(left);
-        } while (!rem.empty());
+        } while (!rem.empty() || (P.kraus && kin_nq));  // damping: a closing pass applies the last choice
         lv.pass_end = (uint32_t)P.passes.size();
     }
 
@@ -1010,6 +1077,8 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
             else if (in.op == OP_DENSE2)
                 need |= (1u << in.p0) | (1u << in.p1);
         }
+        if (fin.kin_nq)
+            need |= (1u << fin.kin_p0) | (1u << fin.kin_p1);
         choose_tile(n, tmax, need, pf.data(), std::min<uint32_t>(n, kMaxGamma), fin);
         uint8_t pos[32];
         std::memset(pos, 0xff, sizeof(pos));
@@ -1051,7 +1120,7 @@ std::string build_plan(const Circuit &c, const Noise &nz, uint64_t shots, const 
     for (uint32_t r = 0; r < S.gamma; r++)
         if (S.rank_q[r] != r)
             return "internal: sampler layout invariant broken";
-    P.fuse = (o.flags & TQS_FLAG_FUSE) != 0;
+    P.fuse = (o.flags & TQS_FLAG_FUSE) != 0 && !P.kraus;
     sink_diagonals(P);
     compile_programs(P);
     return "";

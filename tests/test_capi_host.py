@@ -116,3 +116,43 @@ def test_ucp_xcp_explicit_baseline(orc):
     assert tqs.tqs_partition(c, nz, 777, tqs.options(mode="baseline")) == ([777], [0, G])
     ex = tqs.options(arity=[4, 3, 2], split=[0, 5, 5, G])
     assert tqs.tqs_partition(c, nz, 20, ex) == ([4, 3, 2], [0, 5, 5, G])
+
+
+def test_noise_model_ex_validation():
+    tqs.tqs_noise_model_ex(1e-3, 1e-2, 2e-2, 0.01, 0.01, 50e-6, 70e-6, 1e-6, 2e-6)
+    bad = (dict(ad_gamma=1.5), dict(pd_lambda=-0.1), dict(t1=50e-6, t2=120e-6, time_1q=1e-6),
+           dict(t1=50e-6, t2=0.0), dict(time_2q=-1.0))
+    for kw in bad:
+        with pytest.raises(capi.TqsError) as e:
+            tqs.tqs_noise_model_ex(1e-3, 1e-2, 2e-2, **kw)
+        assert e.value.status == capi.TQS_EINVAL, kw
+
+
+def test_damping_plan_keeps_circuit_order_one_gate_per_pass():
+    """With damping channels every gate's choice needs the state after it, so the
+    plan keeps circuit order, one gate per tile pass, plus one closing pass per
+    level that applies the last gate's choice."""
+    circ = qft(6)
+    G = len(circ.gates)
+    c = tqs.circuit(circ)
+    nz = tqs.tqs_noise_model_ex(1e-3, 1e-2, 2e-2, ad_gamma=0.01)
+    o = tqs.options(arity=[8, 2, 4], split=[0, G // 3, 2 * G // 3, G])
+    order, passes, tiles = tqs.tqs_debug_plan_order(c, nz, 64, o, G)
+    assert list(order) == list(range(G))
+    assert len(tiles) == G + 3
+    plain = tqs.tqs_noise_model(1e-3, 1e-2, 2e-2)
+    _, _, tiles_plain = tqs.tqs_debug_plan_order(c, plain, 64, o, G)
+    assert len(tiles_plain) < G
+
+
+def test_dcp_counts_damping_in_the_error_rate(orc):
+    """DCP's first-subcircuit error estimate includes the damping rates; the
+    library's tree equals the oracle partitioner's with the same rates."""
+    circ = qft(12)
+    kr = orc.core.kraus_params(ad=0.01, pd=0.01)
+    arity, split, _ = orc.partition.dcp(orc.partition.gate_rates(circ, 1e-3, 1e-2, kr), 4000)
+    c = tqs.circuit(circ)
+    nz = tqs.tqs_noise_model_ex(1e-3, 1e-2, 2e-2, ad_gamma=0.01, pd_lambda=0.01)
+    assert tqs.tqs_partition(c, nz, 4000, tqs.options()) == (arity, split)
+    a_plain, _, _ = orc.partition.dcp(orc.partition.gate_rates(circ, 1e-3, 1e-2), 4000)
+    assert arity[0] >= a_plain[0]
