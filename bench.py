@@ -245,6 +245,9 @@ def main():
                     help="shots per step (smaller values make the small case of a profiler capture)")
     ap.add_argument("--batch", type=int, default=0,
                     help="tree nodes per launch (0: the library's choice)")
+    ap.add_argument("--arity", default="",
+                    help="comma-separated tree arities overriding DCP (with --shots below the workload's, the "
+                         "small case of a profiler capture runs the workload's own tree); split: equal gate counts")
     args = ap.parse_args()
     dist, world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -272,7 +275,15 @@ def main():
 
     SH = args.shots
 
+    tree_kw = {}
+    if args.arity:
+        ar = [int(x) for x in args.arity.split(",")]
+        G = len(circ.gates)
+        tree_kw = {"arity": ar, "split": [G * i // len(ar) for i in range(len(ar) + 1)]}
+
     def make_plan(shots, **kw):
+        if kw.get("mode") != "baseline":
+            kw = {**tree_kw, **kw}
         o = tqs.options(stream=stream.cuda_stream, batch=args.batch, **kw)
         probe = tqs.tqs_plan_create(c, nz, shots, o)
         nbytes = tqs.tqs_plan_workspace_bytes(probe)

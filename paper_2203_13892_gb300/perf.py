@@ -14,6 +14,10 @@ headline one (which bench.py measures): one JSON line per configuration.
   qft20_host     the 20-qubit QFT, 32,000 shots, tree FP32, with the state pool
                  in device memory and in mapped host memory (not in the default
                  list)
+  batch64_serial the batch64 circuits as 64 plans run back to back on one stream
+  rc16_fused / rc20_fused
+                 random 16x40 / 20x40 circuits, 8,192 shots, tree FP32 with and
+                 without the fused tensor-core blocks
 
 Device time comes from the library's CUDA events (report.kernel_ms); noise
 p1 = 1e-3, p2 = 1e-2, pm = 2e-2 throughout.  Inputs are synthetic circuits of
@@ -85,6 +89,54 @@ def batch64(reps, autotune):
             "shots_per_s": total / (best * 1e-3), "graph_replay": True, "create_s": create_s}
 
 
+def batch64_serial(reps):
+    """The batch64 circuits as 64 separate plans executed back to back on one
+    stream (no graph): the comparison for the graph-branch batch."""
+    import torch
+
+    spec = batch_circuits_spec()
+    circs = [random_layers(n, L, seed) for n, L, seed in spec]
+    noises = [capi.tqs_noise_model(*NOISE) for _ in circs]
+    stream = torch.cuda.Stream()
+    plans, counts = [], []
+    for c, nz in zip(circs, noises):
+        o = capi.options(prec="fp32", stream=stream.cuda_stream, workspace_bytes=2 << 30)
+        plans.append(capi.tqs_plan_create(capi.circuit(c), nz, 2048, o))
+        counts.append(torch.zeros(1 << c.n, dtype=torch.int64, device="cuda"))
+    def run(seed0):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            for i, (p, d) in enumerate(zip(plans, counts)):
+                capi.tqs_plan_execute(p, seed0 + i, d.data_ptr())
+            b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b)
+    run(0)
+    best = min(run(1000 * (r + 1)) for r in range(reps))
+    for p in plans:
+        p.close()
+    return {"config": "batch64_serial", "circuits": len(circs), "shots_each": 2048, "ms": best,
+            "shots_per_s": 2048 * len(circs) / (best * 1e-3), "graph_replay": False}
+
+
+def fused(name, circ, shots, reps):
+    """Tree FP32 with and without the fused tensor-core blocks (TQS_FLAG_FUSE)."""
+    c, nz = capi.circuit(circ), capi.tqs_noise_model(*NOISE)
+    d = _device_counts(circ.n)
+    out = {"config": name, "n": circ.n, "gates": len(circ.gates), "shots": shots}
+    for label, flags in (("per_gate", 0), ("fused", capi.TQS_FLAG_FUSE)):
+        plan = capi.tqs_plan_create(c, nz, shots, capi.options(prec="fp32", flags=flags | capi.TQS_FLAG_PROFILE))
+        capi.tqs_plan_execute(plan, 0, d.data_ptr())
+        reps_ = [capi.tqs_plan_execute(plan, 1 + r, d.data_ptr(), report=True) for r in range(reps)]
+        best = min(r["kernel_ms"] for r in reps_)
+        out[label] = {"ms": best, "shots_per_s": shots / (best * 1e-3), "fused_blocks": reps_[-1]["fused_blocks"],
+                      "passes": reps_[-1]["passes"]}
+        plan.close()
+    out["fused_over_per_gate"] = out["fused"]["shots_per_s"] / out["per_gate"]["shots_per_s"]
+    return out
+
+
 def host_pool(name, circ, shots, reps):
     """Tree FP32 with the state pool in device memory and in mapped host memory
     (TQS_FLAG_HOST_POOL: the pass kernels read parents from and write children
@@ -125,6 +177,12 @@ def main(argv=None):
             r = host_pool(name, qft(20), 32000, a.reps)
         elif name == "batch64":
             r = batch64(a.reps, a.autotune)
+        elif name == "batch64_serial":
+            r = batch64_serial(a.reps)
+        elif name == "rc16_fused":
+            r = fused(name, random_layers(16, 40, 16040), 8192, a.reps)
+        elif name == "rc20_fused":
+            r = fused(name, random_layers(20, 40, 20040), 8192, a.reps)
         else:
             raise SystemExit(f"unknown config {name}")
         print(json.dumps(r), flush=True)
