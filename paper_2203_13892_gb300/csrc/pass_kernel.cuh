@@ -561,6 +561,18 @@ template <int LOGR>
 __device__ __forceinline__ void acc_flush(DiagAcc<float2, LOGR> &A, float2 (&v)[1 << LOGR], uint32_t msig)
 {
     constexpr int NR = 1 << LOGR;
+    if (A.e_used == 0u && A.gs_used == 0u) {
+        // the common case of runs on thread and outside-tile bits only: one
+        // phase per thread, whatever the frame mask
+        if (A.base_used) {
+            const float2 eb = expi_turn(A.base);
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                v[k] = cmul(v[k], eb);
+        }
+        A.reset();
+        return;
+    }
     constexpr int NP = LOGR > 1 ? LOGR * (LOGR - 1) / 2 : 1;
     uint32_t B = A.base;
     uint32_t E[LOGR > 0 ? LOGR : 1], G[NP];
@@ -708,9 +720,13 @@ template <typename C> __device__ __forceinline__ C shfl_xor_c(C a, int m)
 // FUSE: the pass holds REC_FUSED records (FP32 tiles of 2^11 or 2^12 only); a
 // separate instantiation so that the tensor-core code does not weigh on the
 // register allocation of the passes without fused gates.
+// The fused instantiations hold about 107 KB of shared memory per CTA (tile,
+// TF32 hi/lo operands), so at most two fit an SM: they are given the registers
+// of two CTAs instead of spilling to fit four.
 template <typename R, int MODE, int LOGR, bool FUSE>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP32_MIN_CTAS : (LOGR == 3 ? 3 : 4))
-                                                           : (LOGR >= 3 ? 1 : 2))
+__global__ void __launch_bounds__(kThreads, FUSE ? 2
+                                            : sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP32_MIN_CTAS : (LOGR == 3 ? 3 : 4))
+                                                             : (LOGR >= 3 ? 1 : 2))
     pass_kernel(const __grid_constant__ PassK a)
 {
     using C = typename CT<R>::T;
@@ -1302,6 +1318,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP
                             acc.mul_base(rh.g0);
                         const uint2 *en = reinterpret_cast<const uint2 *>(pay + 80);
                         const uint32_t nb = rh.nbase;
+                        if (rh.pad[0]) {  // base entries only (no slot terms): the usual run in the leaves
+                            if (nb)
+                                acc.base_used = true;
+                            uint32_t add = 0;  // (the run's global phase was added above)
+                            for (uint32_t i = 0; i < nb; i++) {
+                                const uint2 e = en[i];
+                                if ((xt & e.x) == e.x)
+                                    add += e.y;
+                            }
+                            acc.base += add;
+                            pending = true;
+                            p += 96u + (nent * 8u + 15u) / 16u * 16u + ngates * ES;
+                            continue;
+                        }
                         if (nb) {
                             acc.base_used = true;
                             uint32_t add = 0;

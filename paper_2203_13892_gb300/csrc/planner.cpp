@@ -758,6 +758,10 @@ static void compile_programs(PlanHost &P)
                     rh.ne[q] = (uint8_t)lists[1 + q].size();
                 rh.gused = (uint16_t)gused;
                 rh.eused = (uint8_t)eused;
+                bool slot_terms = gused || eused;
+                for (uint32_t q = 0; q < kMaxSlots; q++)
+                    slot_terms = slot_terms || !lists[1 + q].empty();
+                rh.pad[0] = slot_terms ? 0 : 1;
                 rh.g0 = turn32(G);
                 for (uint32_t q = 0; q < kMaxSlots; q++)
                     rh.econst[q] = econst[q];
