@@ -725,7 +725,7 @@ template <typename C> __device__ __forceinline__ C shfl_xor_c(C a, int m)
 // of two CTAs instead of spilling to fit four.
 template <typename R, int MODE, int LOGR, bool FUSE>
 __global__ void __launch_bounds__(kThreads, FUSE ? 2
-                                            : sizeof(R) == 4 ? (LOGR >= 4 ? TQS_FP32_MIN_CTAS : (LOGR == 3 ? 3 : 4))
+                                            : sizeof(R) == 4 ? (LOGR >= 5 ? 2 : LOGR == 4 ? TQS_FP32_MIN_CTAS : (LOGR == 3 ? 3 : 4))
                                                              : (LOGR >= 3 ? 1 : 2))
     pass_kernel(const __grid_constant__ PassK a)
 {
