@@ -119,7 +119,8 @@ struct RunHdr32 {
     uint8_t ne[kMaxSlots];
     uint16_t gused;            // pairs with a nonzero phase
     uint8_t eused;             // slots with a nonzero econst
-    uint8_t pad[7];            // pad[0] = 1: only base entries (no slot term at all)
+    uint8_t pad[7];            // pad[0] = 1: only base entries (no slot term at all);
+                               // pad[1] = all entries (nbase + sum of ne)
     uint32_t g0;               // global phase of the run
     uint32_t econst[kMaxSlots];
     uint32_t gp[kMaxSlots * (kMaxSlots - 1) / 2];

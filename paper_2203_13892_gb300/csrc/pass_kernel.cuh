@@ -1303,10 +1303,7 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
                     // FP32 run: phases grouped by accumulator (RunHdr32), no per-factor
                     // dispatch; a node with a Pauli inside the run goes gate by gate
                     const RunHdr32 &rh = *reinterpret_cast<const RunHdr32 *>(pay);
-                    uint32_t nent = rh.nbase;
-#pragma unroll
-                    for (int q = 0; q < (int)kMaxSlots; q++)
-                        nent += rh.ne[q];
+                    const uint32_t nent = rh.pad[1];
                     constexpr uint32_t ES = 16u + 4u * (uint32_t)sizeof(V);  // GateEnt + 4 phases
                     const unsigned char *gents = pay + 80 + (nent * 8u + 15u) / 16u * 16u;
                     const uint32_t ngates = hiend - hibeg;

@@ -489,7 +489,7 @@ static void compile_programs(PlanHost &P)
     const bool f64 = P.prec == TQS_FP64;
     // FP64: diagonal factors are complex doubles; FP32: phases (turn32), 4 bytes
     const size_t csz = f64 ? 16 : 8, fsz = f64 ? 32 : 16, esz = 16 + 4 * (f64 ? csz : 4);
-    const size_t kMaxFactors = 200;
+    const size_t kMaxFactors = 200;  // also keeps an FP32 run's entry count within RunHdr32's byte
     std::vector<uint8_t> &out = P.prog;
     out.clear();
     P.chunk_off.clear();
@@ -762,6 +762,7 @@ static void compile_programs(PlanHost &P)
                 for (uint32_t q = 0; q < kMaxSlots; q++)
                     slot_terms = slot_terms || !lists[1 + q].empty();
                 rh.pad[0] = slot_terms ? 0 : 1;
+                rh.pad[1] = (uint8_t)nent;
                 rh.g0 = turn32(G);
                 for (uint32_t q = 0; q < kMaxSlots; q++)
                     rh.econst[q] = econst[q];

@@ -83,3 +83,43 @@ def test_learned_partition_uses_model_and_respects_dcp():
         assert int(counts.sum()) == shots
     finally:
         tqs.tqs_learned_set_model(None)
+
+
+def test_committed_model_against_dcp_on_held_out_circuits():
+    """What the trained network gains over the paper's partitioner: on eight
+    held-out circuits of the evaluation set (20-22 qubits, seeds 200000+i), the
+    committed model's trees against DCP's, each timed on whole level-0 subtrees
+    (best of two after a warm-up), and the normalised-fidelity difference of
+    full 2,048-shot runs.  Every learned tree keeps DCP's guarantees (first-level
+    sample at least DCP's, no more levels); the measured speed ratio must not be
+    a loss of more than 5 % on average, and the fidelity difference stays within
+    the paper's largest tree-vs-baseline difference (0.016, Sec. 5.4) plus the
+    spread of a 2,048-shot estimate.  The numbers are printed: the model's gain
+    over DCP is small by design (it chooses among trees DCP allows)."""
+    from paper_2203_13892_gb300 import learned
+
+    w = learned.load_model()
+    tqs.tqs_learned_set_model(w)
+    try:
+        ratios, dF = [], []
+        for i in range(8):
+            circ = learned.training_circuit(i, 200000, (20, 22), (20, 60))
+            c, nz = tqs.circuit(circ), tqs.tqs_noise_model(*learned.NOISE)
+            trees = {}
+            for part in ("dcp", "learned"):
+                trees[part] = tqs.tqs_partition(c, nz, 8192, tqs.options(part=part))
+            (ad, _), (al, _) = trees["dcp"], trees["learned"]
+            assert al[0] >= ad[0] and len(al) <= len(ad)
+            t = {p: learned.time_tree(c, nz, 8192, a, s, "fp32", learned.trial_leaves_for(circ.n), reps=2, warmup=1)
+                 for p, (a, s) in trees.items()}
+            ratios.append(t["dcp"] / t["learned"])
+            F = {}
+            for part in ("dcp", "learned"):
+                _, F[part], _ = tqs.tqs_simulate(c, nz, 2048, 11, tqs.options(part=part), n=circ.n)
+            dF.append(abs(F["learned"] - F["dcp"]))
+        print(f"learned/DCP speed: mean {np.mean(ratios):.3f} min {np.min(ratios):.3f} max {np.max(ratios):.3f}; "
+              f"|F_learned - F_dcp|: mean {np.nanmean(dF):.4f} max {np.nanmax(dF):.4f}")
+        assert np.mean(ratios) >= 0.95, ratios
+        assert np.nanmax(dF) <= 0.05, dF
+    finally:
+        tqs.tqs_learned_set_model(None)
