@@ -75,10 +75,13 @@ uint64_t shape_key(const tqs_circuit *c, const tqs_options &o, uint64_t shots)
 }
 }  // namespace
 
-// Picks tile_qubits (and, for FP32, whether dense blocks are fused onto the
-// tensor cores) for this circuit shape: each candidate runs the same tree on a
-// few whole level-0 subtrees and the fastest per leaf wins.  The cache holds
-// tile_qubits | (fuse << 8); a caller that set TQS_FLAG_FUSE keeps it.
+// Picks tile_qubits (how many qubits a tile pass holds: the split between the
+// low, in-tile qubits and the high ones gathered per tile), for FP32 whether
+// dense blocks are fused onto the tensor cores, and then the node batch (tree
+// nodes per launch) for this circuit shape: each candidate runs the same tree on
+// a few whole level-0 subtrees and the fastest per leaf wins.  The cache holds
+// tile_qubits | (fuse << 8) | (batch << 16) (batch 0: the library's choice); a
+// caller that set TQS_FLAG_FUSE keeps it, one that set batch keeps it.
 tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options &o,
                     tqs_options &tuned)
 {
@@ -88,8 +91,10 @@ tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, c
     const uint64_t key = shape_key(c, o, shots);
     auto apply = [&](uint32_t v) {
         tuned.tile_qubits = v & 0xffu;
-        if (v >> 8)
+        if ((v >> 8) & 1u)
             tuned.flags |= TQS_FLAG_FUSE;
+        if (!o.batch && (v >> 16))
+            tuned.batch = v >> 16;
     };
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -122,25 +127,19 @@ tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, c
             if (t <= n)
                 cands.push_back(t | 0x100u);
     const uint32_t fuse_all = (o.flags & TQS_FLAG_FUSE) ? 0x100u : 0u;
-    uint32_t best = 0;
-    double best_t = 1e300;
-    bool small_done = false;
-    for (uint32_t cand : cands) {
-        const uint32_t t = cand & 0xffu;
-        if (t > n) {  // every width >= n gives the same single-tile plan
-            if (small_done)
-                continue;
-            small_done = true;
-        }
+    // one trial: the device time of two runs of the trial tree (the second kept)
+    auto trial = [&](uint32_t cand, float &ms) -> tqs_status {
         tqs_options tr = o;
         tr.flags &= ~(TQS_FLAG_AUTOTUNE | TQS_FLAG_PROFILE);
-        if (cand >> 8)
+        if ((cand >> 8) & 1u)
             tr.flags |= TQS_FLAG_FUSE;
+        if (cand >> 16)
+            tr.batch = cand >> 16;
         tr.part = TQS_PART_EXPLICIT;
         tr.k = (uint32_t)arity.size() - 1;
         tr.arity = arity.data();
         tr.split = split.data();
-        tr.tile_qubits = t;
+        tr.tile_qubits = cand & 0xffu;
         tr.workspace = nullptr;
         tr.workspace_bytes = o.workspace ? 0 : o.workspace_bytes;
         std::unique_ptr<tqs_plan> p;
@@ -148,7 +147,6 @@ tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, c
         if (st != TQS_OK)
             return st;
         std::string err;
-        float ms = 0;
         for (int rep = 0; rep < 2; rep++) {
             st = p->dp.execute(rep, p->dp.d_counts_internal, true, err);
             if (st != TQS_OK)
@@ -159,9 +157,40 @@ tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, c
             if (e != cudaSuccess)
                 return set_error(TQS_ECUDA, cuda_msg("autotune trial", (int)e));
         }
+        return TQS_OK;
+    };
+    uint32_t best = 0;
+    double best_t = 1e300;
+    bool small_done = false;
+    // first the tile width (and fusion) ...
+    for (uint32_t cand : cands) {
+        const uint32_t t = cand & 0xffu;
+        if (t > n) {  // every width >= n gives the same single-tile plan
+            if (small_done)
+                continue;
+            small_done = true;
+        }
+        float ms = 0;
+        tqs_status st = trial(cand, ms);
+        if (st != TQS_OK)
+            return st;
         if (ms < best_t) {
             best_t = ms;
             best = cand | fuse_all;
+        }
+    }
+    // ... then the node batch with that width (the library's default is the first candidate)
+    if (!o.batch) {
+        const uint32_t width = best & 0xffffu;
+        for (uint32_t b : {32u, 64u, 128u, 512u}) {
+            float ms = 0;
+            tqs_status st = trial(width | (b << 16), ms);
+            if (st != TQS_OK)
+                return st;
+            if (ms < best_t) {
+                best_t = ms;
+                best = width | (b << 16);
+            }
         }
     }
     {
