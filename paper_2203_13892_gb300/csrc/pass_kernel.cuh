@@ -389,16 +389,16 @@ template <int NS> struct DiagAcc<float2, NS> {
     }
 };
 
-// exp(2 pi i a / 2^32) for a phase a in units of 2^-32 turns.  The angle is
-// rounded to 2^-23 turns (at most 3.7e-7 rad), taken into [-pi, pi) as a
-// signed integer, converted exactly with the 1.5 * 2^23 float trick, and passed
-// to the hardware sine and cosine (absolute error about 4e-7 on [-pi, pi]).
+// exp(2 pi i a / 2^32) for a phase a in units of 2^-32 turns.  The phase is
+// taken into [-pi, pi) as a signed integer and converted to float (rounded to
+// 24 bits: at most 1e-7 rad off), then passed to the hardware sine and cosine
+// (absolute error about 4e-7 on [-pi, pi]).  The conversion runs on the
+// transcendental unit, which the passes leave mostly idle, not on the integer
+// pipe they saturate.
 __device__ __forceinline__ float2 expi_turn(uint32_t a)
 {
-    const int32_t ai = (int32_t)(a + 256u) >> 9;
-    const float f = __int_as_float(ai + 0x4B400000) - 12582912.0f;
     float sn, cs;
-    __sincosf(f * 7.4901405e-07f, &sn, &cs);  // 2 pi / 2^23
+    __sincosf((float)(int32_t)a * 1.4629181e-09f, &sn, &cs);  // 2 pi / 2^32
     return make_float2(cs, sn);
 }
 
@@ -407,16 +407,6 @@ __device__ __forceinline__ uint32_t turn_of(float re, float im)
 {
     const double t = (double)atan2f(im, re) * (4294967296.0 / 6.283185307179586);
     return (uint32_t)(int64_t)llrint(t);
-}
-
-// registers whose index has bit s set (NR = 2^LOGR registers)
-template <int LOGR> __device__ __forceinline__ constexpr uint32_t reg_pattern(int s)
-{
-    uint32_t m = 0;
-    for (int k = 0; k < (1 << LOGR); k++)
-        if ((k >> s) & 1)
-            m |= 1u << k;
-    return m;
 }
 
 // tile position j: thread bit (j < 8 or tile smaller than the CTA), slot bit s = j-8, or outside (0xff)
