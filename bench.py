@@ -63,29 +63,34 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(kernels="generic"):
     """Hash of the files the pass kernel is compiled and launched from: its six
     instantiation units, the headers of csrc they include, and kernels.cu (which
-    sets its grid and shared memory).  Host-only sources do not enter."""
+    sets its grid and shared memory); for the specialised kernels also the
+    generator that writes their statements (specialize.cpp).  Host-only sources
+    do not enter."""
     d = os.path.join(ROOT, "paper_2203_13892_gb300", "csrc")
     names = sorted(f for f in os.listdir(d) if f.startswith("pass_") and f.endswith(".cu"))
     names += ["pass_kernel.cuh", "pass_kernel.h", "device_common.cuh", "internal.h", "kernels.cu"]
+    if kernels == "specialized":
+        names += ["specialize.cpp", "specialize.h"]
     h = hashlib.sha256()
     for f in names:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kind, alg_bytes_per_launch):
+def recorded_traffic(kind, alg_bytes_per_launch, kernels="generic"):
     """DRAM bytes per launch of kernel class `kind`, from the committed ncu
     capture of a small case of the same kernel: its DRAM bytes per CTA (one
     tile of one node) times the CTAs of a full launch, or None when the kernels
     changed since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "traffic_qft20_tree_fp32.json")
+    name = "traffic_qft20_tree_fp32" + ("_specialized" if kernels == "specialized" else "") + ".json"
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("source_hash") != kernel_source_hash():
+    if d.get("source_hash") != kernel_source_hash(kernels):
         return None
     ent = d.get("kernels", {}).get(kind)
     if not ent:
@@ -245,6 +250,9 @@ def main():
                     help="shots per step (smaller values make the small case of a profiler capture)")
     ap.add_argument("--batch", type=int, default=0,
                     help="tree nodes per launch (0: the library's choice)")
+    ap.add_argument("--kernels", default="specialized", choices=["specialized", "generic"],
+                    help="FP32 tree pass kernels: compiled per pass program at plan time (TQS_FLAG_SPECIALIZE), "
+                         "or the generic kernel that interprets the pass programs")
     ap.add_argument("--arity", default="",
                     help="comma-separated tree arities overriding DCP (with --shots below the workload's, the "
                          "small case of a profiler capture runs the workload's own tree); split: equal gate counts")
@@ -293,7 +301,10 @@ def main():
         o.workspace_bytes = nbytes
         return tqs.tqs_plan_create(c, nz, shots, o), ws
 
-    plan, ws = make_plan(SH, flags=capi.TQS_FLAG_PROFILE)
+    spec_flag = capi.TQS_FLAG_SPECIALIZE if args.kernels == "specialized" else 0
+    t_plan = time.perf_counter()
+    plan, ws = make_plan(SH, flags=capi.TQS_FLAG_PROFILE | spec_flag)
+    plan_create_s = time.perf_counter() - t_plan  # includes compiling the specialised kernels (first use)
     d_counts = torch.zeros(1 << N_QUBITS, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -393,7 +404,7 @@ def main():
     baseline["frac_of_peak"] = baseline["pass_GBps"] / peak
 
     # ---- end to end through the public call with host buffers --------
-    o = tqs.options(stream=stream.cuda_stream, batch=args.batch)
+    o = tqs.options(stream=stream.cuda_stream, batch=args.batch, flags=spec_flag)
     o.workspace = ws.data_ptr()
     o.workspace_bytes = ws.numel()
     del plan
@@ -429,10 +440,14 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(rep0["arity"], rep0["split"],
                                   {"parallelism": f"independent problem per GPU x{world}",
-                                   "passes_per_level": rep0["passes"]}, SH),
+                                   "passes_per_level": rep0["passes"], "plan_create_s": round(plan_create_s, 2),
+                                   "pass_kernels": ("specialised per pass program (NVRTC, sm_103a), compiled at plan "
+                                                    "creation, outside the timed region" if args.kernels == "specialized"
+                                                    else "generic (interprets the pass programs)")}, SH),
         "roofline": {"bound": "hbm", "kernel": f"pass_kernel[{dom}]", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic(dom, per_launch_bytes), "alg_bytes_per_launch": per_launch_bytes,
+                     "traffic": recorded_traffic(dom, per_launch_bytes, args.kernels),
+                     "alg_bytes_per_launch": per_launch_bytes,
                      "avg_launch_ms": avg_s * 1e3, "launches": D["launches"]},
         "kernel_classes": {n: {"launches": d["launches"], "ms_per_step": d["ms"] / args.steps,
                                "GBps": (d["bytes"] / (d["ms"] * 1e-3) / 1e9) if d["ms"] > 0 else None}

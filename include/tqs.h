@@ -156,6 +156,17 @@ typedef enum {
                                         kernels that the output pool holds one slot fewer than it does,
                                         so the last node of a full launch fails the check above (no
                                         access is made out of range) */
+#define TQS_FLAG_SPECIALIZE 0x100u  /* FP32 plans: compile, when the plan is created, one pass kernel per
+                                       pass program (NVRTC, sm_103a): the pass's records become
+                                       straight-line code with its tile layout as constants, in place
+                                       of the generic kernel that interprets them.  Same arithmetic,
+                                       fewer instructions; a few seconds of compilation per new
+                                       circuit (kept for the life of the process, keyed by the
+                                       program).  Passes with fused tensor-core blocks keep the
+                                       generic kernel; FP64 plans ignore the flag.  Needs NVRTC
+                                       (libnvrtc.so.13) and the driver at run time, else
+                                       TQS_EUNSUPPORTED; refused by tqs_simulate_static, which must
+                                       not allocate. */
 
 /* Kernel classes timed under TQS_FLAG_PROFILE (index into report.prof_*). */
 #define TQS_PROF_NOISE 0   /* Philox noise draws + Pauli frames */
@@ -327,6 +338,24 @@ tqs_status tqs_debug_node_noise(const tqs_circuit *c, const tqs_noise *nz, uint6
 tqs_status tqs_debug_plan_order(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots,
                                 const tqs_options *opts, uint32_t *order_out, uint32_t *pass_out,
                                 uint32_t *tile_out, uint32_t *npasses_out);
+/* tqs_debug_spec_check (host only, no device call): builds the plan the options
+ * select (FP32), generates the source of every kernel TQS_FLAG_SPECIALIZE would
+ * compile for it and compiles each with NVRTC for sm_103a without loading it.
+ * *nkernels_out = the kernels generated (passes with fused tensor-core blocks
+ * have none); *src_bytes_out (optional) = their total generated source.  Returns
+ * TQS_EUNSUPPORTED without NVRTC, TQS_EINVAL for FP64 options, TQS_ECUDA with
+ * the compiler's log (tqs_last_error) if a kernel does not compile. */
+tqs_status tqs_debug_spec_check(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots,
+                                const tqs_options *opts, uint32_t *nkernels_out, uint64_t *src_bytes_out);
+/* tqs_debug_spec_source (host only): the generated source of global pass `pass`
+ * in mode `mode` (0 store, 1 sums, 2 sample): the tile-layout constants, then
+ * the pass's records as statements, NUL-terminated in the HOST buffer `buf` of
+ * `cap` bytes (truncated to fit); *len_out = the full length.  TQS_EINVAL for
+ * a pass index out of range or FP64 options, TQS_EUNSUPPORTED when the pass has
+ * no specialised form (fused tensor-core blocks). */
+tqs_status tqs_debug_spec_source(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots,
+                                 const tqs_options *opts, uint32_t pass, int mode, char *buf, uint64_t cap,
+                                 uint64_t *len_out);
 
 /* Simulation without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory, such as

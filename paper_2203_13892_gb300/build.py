@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtqs.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", OUT]
 
 
 def nvcc() -> str:
@@ -34,8 +34,34 @@ def _headers():
             glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
+# The headers the specialised pass kernels are compiled from at run time (NVRTC),
+# embedded into the library as string literals.
+JIT_HEADERS = ["internal.h", "device_common.cuh", "pass_kernel.h", "pass_kernel.cuh"]
+JIT_INC = os.path.join(OUT, "tqs_jit_sources.inc")
+
+
+def _write_jit_sources() -> None:
+    delim = "tqsjit"
+    names, texts = [], []
+    for h in JIT_HEADERS:
+        text = open(os.path.join(CSRC, h)).read()
+        if ")" + delim + '"' in text:
+            raise RuntimeError(f"{h} contains the raw-string delimiter")
+        names.append(f'"{h}"')
+        texts.append(f'R"{delim}({text}){delim}"')
+    body = ("// generated by build.py from the csrc headers the specialised pass kernels include\n"
+            f"static const char *const kJitNames[] = {{{', '.join(names)}}};\n"
+            f"static const char *const kJitTexts[] = {{\n" + ",\n".join(texts) + "};\n")
+    if not os.path.exists(JIT_INC) or open(JIT_INC).read() != body:
+        tmp = JIT_INC + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            f.write(body)
+        os.replace(tmp, JIT_INC)
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
+    _write_jit_sources()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdr_time = max((os.path.getmtime(h) for h in _headers()), default=0.0)
     cc = nvcc()
@@ -61,7 +87,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             list(ex.map(run, jobs))
     if jobs or force or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([cc] + ARCH + ["-shared", "-o", tmp] + objs)
+        run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -28,6 +28,7 @@ TQS_FLAG_HOST_POOL = 0x10
 TQS_FLAG_DEBUG_BOUNDS = 0x20
 TQS_FLAG_FAULT_TIMEOUT = 0x40
 TQS_FLAG_FAULT_BOUNDS = 0x80
+TQS_FLAG_SPECIALIZE = 0x100
 TQS_MAX_LEVELS = 17
 TQS_PROF_KINDS = 4
 PROF_NAMES = ("noise", "store", "sums", "sample")
@@ -98,7 +99,9 @@ EXPORTS = (
     "tqs_circuit_create", "tqs_circuit_destroy", "tqs_noise_model", "tqs_noise_model_ex", "tqs_noise_destroy",
     "tqs_options_default", "tqs_partition", "tqs_simulate", "tqs_plan_create",
     "tqs_plan_execute", "tqs_plan_workspace_bytes", "tqs_plan_host_pool_bytes", "tqs_plan_destroy",
-    "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_debug_plan_order", "tqs_simulate_static",
+    "tqs_debug_node_state", "tqs_debug_node_noise", "tqs_debug_plan_order", "tqs_debug_spec_check",
+    "tqs_debug_spec_source",
+    "tqs_simulate_static",
     "tqs_last_error",
     "tqs_abi_version", "tqs_batch_create", "tqs_batch_execute", "tqs_batch_counts",
     "tqs_batch_device_counts", "tqs_batch_size", "tqs_batch_destroy", "tqs_learned_param_count",
@@ -153,6 +156,12 @@ def lib():
             u32p = C.POINTER(C.c_uint32)
             L.tqs_debug_plan_order.argtypes = [vp, vp, C.c_uint64, C.POINTER(tqs_options), u32p, u32p, u32p, u32p]
             L.tqs_debug_plan_order.restype = st
+            L.tqs_debug_spec_check.argtypes = [vp, vp, C.c_uint64, C.POINTER(tqs_options), u32p,
+                                               C.POINTER(C.c_uint64)]
+            L.tqs_debug_spec_check.restype = st
+            L.tqs_debug_spec_source.argtypes = [vp, vp, C.c_uint64, C.POINTER(tqs_options), C.c_uint32, C.c_int,
+                                                C.c_char_p, C.c_uint64, C.POINTER(C.c_uint64)]
+            L.tqs_debug_spec_source.restype = st
             L.tqs_simulate_static.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.POINTER(tqs_options), vp]
             L.tqs_simulate_static.restype = st
             L.tqs_batch_create.argtypes = [C.c_size_t, C.POINTER(vp), C.POINTER(vp), u64p, C.POINTER(tqs_options),
@@ -380,6 +389,29 @@ def tqs_debug_plan_order(c: Handle, nz: Handle, shots: int, opts: Optional[tqs_o
                                       order.ctypes.data_as(u32p), pas.ctypes.data_as(u32p),
                                       tiles.ctypes.data_as(u32p), C.byref(npass)))
     return order[:n_gates], pas[:n_gates], tiles[:npass.value]
+
+
+def tqs_debug_spec_check(c: Handle, nz: Handle, shots: int, opts: Optional[tqs_options]) -> Tuple[int, int]:
+    """Host only.  Generates and compiles (NVRTC, not loaded) every specialised
+    pass kernel of the plan; returns (kernels, generated source bytes)."""
+    nk = C.c_uint32()
+    nb = C.c_uint64()
+    _check(lib().tqs_debug_spec_check(c.ptr, nz.ptr, int(shots), C.byref(opts) if opts else None,
+                                      C.byref(nk), C.byref(nb)))
+    return nk.value, nb.value
+
+
+def tqs_debug_spec_source(c: Handle, nz: Handle, shots: int, opts: Optional[tqs_options], pass_index: int,
+                          mode: int) -> str:
+    """Host only.  The generated source (layout constants and statements) of one
+    pass's specialised kernel in mode 0 (store), 1 (sums) or 2 (sample)."""
+    n = C.c_uint64()
+    _check(lib().tqs_debug_spec_source(c.ptr, nz.ptr, int(shots), C.byref(opts) if opts else None,
+                                       int(pass_index), int(mode), None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value + 1)
+    _check(lib().tqs_debug_spec_source(c.ptr, nz.ptr, int(shots), C.byref(opts) if opts else None,
+                                       int(pass_index), int(mode), buf, n.value + 1, C.byref(n)))
+    return buf.value.decode()
 
 
 def tqs_simulate_static(c: Handle, nz: Handle, shots: int, seed: int, opts: Optional[tqs_options],

@@ -1,6 +1,7 @@
 // capi.cpp -- the extern "C" boundary declared in include/tqs.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -10,6 +11,7 @@
 
 #include "executor.h"
 #include "handles.h"
+#include "specialize.h"
 
 namespace {
 thread_local std::string g_err;
@@ -296,6 +298,87 @@ tqs_status tqs_debug_plan_order(const tqs_circuit *c, const tqs_noise *nz, uint6
         }
     }
     *npasses_out = (uint32_t)H.passes.size();
+    return TQS_OK;
+}
+
+tqs_status tqs_debug_spec_check(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
+                                uint32_t *nkernels_out, uint64_t *src_bytes_out)
+{
+    if (!c || !nz || !nkernels_out)
+        return fail(TQS_EINVAL, "NULL argument");
+    if (shots == 0)
+        return fail(TQS_EINVAL, "shots must be >= 1");
+    tqs_options o = opts_or_default(opts);
+    if (o.prec != TQS_FP32)
+        return fail(TQS_EINVAL, "specialised pass kernels are for FP32 plans");
+    const std::string why = tqs::spec_available(false);
+    if (!why.empty())
+        return fail(TQS_EUNSUPPORTED, why);
+    std::vector<uint64_t> arity;
+    std::vector<uint32_t> split;
+    tqs_status st = from_msg(tqs::partition(c->c, nz->nz, shots, o, arity, split));
+    if (st != TQS_OK)
+        return st;
+    tqs::PlanHost H;
+    st = from_msg(tqs::build_plan(c->c, nz->nz, shots, o, arity, split, H));
+    if (st != TQS_OK)
+        return st;
+    std::vector<tqs::SpecSource> srcs;
+    uint64_t bytes = 0;
+    const uint32_t last = H.levels.empty() ? 0 : H.levels.back().pass_end - 1;
+    for (uint32_t pi = 0; pi < (uint32_t)H.passes.size(); pi++)
+        for (int mode : {tqs::MODE_STORE, tqs::MODE_SUMS, tqs::MODE_SAMPLE}) {
+            if (mode != tqs::MODE_STORE && pi != last)
+                continue;
+            tqs::SpecSource s;
+            if (!tqs::spec_generate(H, H.passes[pi], mode, s).empty())
+                continue;
+            bytes += s.defs.size() + s.walk.size();
+            srcs.push_back(std::move(s));
+        }
+    const std::string m = tqs::spec_compile_only(srcs);
+    if (!m.empty())
+        return fail(TQS_ECUDA, m);
+    *nkernels_out = (uint32_t)srcs.size();
+    if (src_bytes_out)
+        *src_bytes_out = bytes;
+    return TQS_OK;
+}
+
+tqs_status tqs_debug_spec_source(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
+                                 uint32_t pass, int mode, char *buf, uint64_t cap, uint64_t *len_out)
+{
+    if (!c || !nz || !len_out)
+        return fail(TQS_EINVAL, "NULL argument");
+    if (shots == 0)
+        return fail(TQS_EINVAL, "shots must be >= 1");
+    if (mode < tqs::MODE_STORE || mode > tqs::MODE_SAMPLE)
+        return fail(TQS_EINVAL, "mode must be 0 (store), 1 (sums) or 2 (sample)");
+    tqs_options o = opts_or_default(opts);
+    if (o.prec != TQS_FP32)
+        return fail(TQS_EINVAL, "specialised pass kernels are for FP32 plans");
+    std::vector<uint64_t> arity;
+    std::vector<uint32_t> split;
+    tqs_status st = from_msg(tqs::partition(c->c, nz->nz, shots, o, arity, split));
+    if (st != TQS_OK)
+        return st;
+    tqs::PlanHost H;
+    st = from_msg(tqs::build_plan(c->c, nz->nz, shots, o, arity, split, H));
+    if (st != TQS_OK)
+        return st;
+    if (pass >= H.passes.size())
+        return fail(TQS_EINVAL, "pass index out of range");
+    tqs::SpecSource s;
+    const std::string why = tqs::spec_generate(H, H.passes[pass], mode, s);
+    if (!why.empty())
+        return fail(TQS_EUNSUPPORTED, why);
+    const std::string text = s.defs + s.walk;
+    *len_out = text.size();
+    if (buf && cap) {
+        const size_t n = std::min<size_t>(text.size(), (size_t)cap - 1);
+        std::memcpy(buf, text.data(), n);
+        buf[n] = '\0';
+    }
     return TQS_OK;
 }
 

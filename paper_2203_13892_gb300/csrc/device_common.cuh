@@ -1,7 +1,9 @@
 // device_common.cuh -- device helpers shared by the kernels of libtqs: the
 // counter-based Philox4x32-10 generator and complex arithmetic.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 
 #include "internal.h"
 

@@ -11,6 +11,7 @@
 #include <string>
 
 #include "executor.h"
+#include "specialize.h"
 
 namespace tqs {
 
@@ -298,6 +299,44 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
     CK(cudaStreamSynchronize(stream));
+    if ((o.flags & TQS_FLAG_SPECIALIZE) && H.prec == TQS_FP32)
+        return build_specialized(err);
+    return TQS_OK;
+}
+
+// TQS_FLAG_SPECIALIZE: one kernel per pass program in the store mode, and the
+// leaf's measuring modes for the last pass of the last level, compiled together.
+tqs_status DevicePlan::build_specialized(std::string &err)
+{
+    const PlanHost &H = host;
+    const std::string why = spec_available();
+    if (!why.empty()) {
+        err = "specialised pass kernels: " + why;
+        return TQS_EUNSUPPORTED;
+    }
+    spec_fn.assign(H.passes.size() * 3, nullptr);
+    std::vector<SpecSource> srcs;
+    std::vector<size_t> slot;
+    const uint32_t last = H.levels.empty() ? 0 : H.levels.back().pass_end - 1;
+    for (uint32_t pi = 0; pi < (uint32_t)H.passes.size(); pi++) {
+        for (int mode : {MODE_STORE, MODE_SUMS, MODE_SAMPLE}) {
+            if (mode != MODE_STORE && pi != last)
+                continue;
+            SpecSource s;
+            if (!spec_generate(H, H.passes[pi], mode, s).empty())
+                continue;  // this pass keeps the generic kernel (fused tensor-core blocks)
+            srcs.push_back(std::move(s));
+            slot.push_back((size_t)pi * 3 + (size_t)mode);
+        }
+    }
+    std::vector<void *> fns;
+    const std::string m = spec_build(srcs, fns);
+    if (!m.empty()) {
+        err = m;
+        return TQS_ECUDA;
+    }
+    for (size_t i = 0; i < slot.size(); i++)
+        spec_fn[slot[i]] = fns[i];
     return TQS_OK;
 }
 
@@ -424,13 +463,16 @@ tqs_status DevicePlan::run_level(uint32_t i, uint64_t lo, uint64_t hi, std::vect
         if (leaf && pl + 1 == np) {
             const double sums = 8.0 * (double)H.samp.groups;
             a.mode = MODE_SUMS;
+            a.spec_fn = spec_for(lv.pass_begin + pl, a.mode);
             CKP(TQS_PROF_SUMS, (double)nn * (rd + sums), launch_pass(a, stream));
             a.mode = MODE_SAMPLE;
+            a.spec_fn = spec_for(lv.pass_begin + pl, a.mode);
             const double blk = rd / (double)((uint64_t)1 << (H.n - ps.t));
             CKP(TQS_PROF_SAMPLE, (double)nn * (sums + blk), launch_pass(a, stream));
             alg_bytes += (double)nn * rd;
         } else {
             a.mode = MODE_STORE;
+            a.spec_fn = spec_for(lv.pass_begin + pl, a.mode);
             CKP(TQS_PROF_STORE, (double)nn * (rd + sb), launch_pass(a, stream));
             alg_bytes += (double)nn * (rd + sb);
             if (ps.kout_gate >= 0)
@@ -547,6 +589,7 @@ tqs_status DevicePlan::run_chain(uint32_t level, uint64_t node, uint64_t seed, s
             a.pass_local = pl;
             a.seed = seed;
             set_kraus(a, ps);
+            a.spec_fn = spec_for(lv.pass_begin + pl, MODE_STORE);
             CKL(launch_pass(a, stream));
             if (ps.kout_gate >= 0)
                 CKL(launch_choice(ps, chain[i], 1, seed, nullptr));

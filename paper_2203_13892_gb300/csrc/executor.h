@@ -51,6 +51,14 @@ struct DevicePlan {
     std::vector<uint8_t *> noise;
     std::vector<NodeMeta *> meta;
     std::vector<uint32_t> pst_host, pst_off;
+    // TQS_FLAG_SPECIALIZE: per pass, the specialised kernel of each mode (nullptr = generic)
+    std::vector<void *> spec_fn;
+    void *spec_for(uint32_t pass, int mode) const
+    {
+        const size_t i = (size_t)pass * 3 + (size_t)mode;
+        return i < spec_fn.size() ? spec_fn[i] : nullptr;
+    }
+    tqs_status build_specialized(std::string &err);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // per-launch profiling (TQS_FLAG_PROFILE)
     struct ProfRec { int kind; double bytes; cudaEvent_t a, b; };

@@ -2,12 +2,25 @@
 // kernels of libtqs (not part of the public ABI; see include/tqs.h).
 #pragma once
 
+// The device-visible part (constants and record layouts) is also compiled at
+// run time by NVRTC for the specialised pass kernels, where no standard header
+// exists: the host-only part is skipped there.
+#ifdef __CUDACC_RTC__
+typedef unsigned char uint8_t;
+typedef signed char int8_t;
+typedef unsigned short uint16_t;
+typedef unsigned int uint32_t;
+typedef int int32_t;
+typedef unsigned long long uint64_t;
+typedef long long int64_t;
+#else
 #include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
 
 #include "../../include/tqs.h"
+#endif
 
 namespace tqs {
 
@@ -45,6 +58,7 @@ struct NodeMeta {
 };
 constexpr uint32_t kMetaNoisy = 0x80000000u;
 
+#ifndef __CUDACC_RTC__
 // ---------------------------------------------------------------------------
 // Host-side circuit and plan
 // ---------------------------------------------------------------------------
@@ -68,6 +82,8 @@ struct Noise {
     double tr_g1 = 0.0, tr_l1 = 0.0, tr_g2 = 0.0, tr_l2 = 0.0;
     bool kraus() const { return ad > 0.0 || pd > 0.0 || tr_g1 > 0.0 || tr_l1 > 0.0 || tr_g2 > 0.0 || tr_l2 > 0.0; }
 };
+
+#endif  // __CUDACC_RTC__
 
 // Compiled pass program: 16-byte aligned records walked in order by every
 // thread of a CTA (uniform).  Record header, then a payload of complex values
@@ -148,6 +164,7 @@ struct FacHdr {
 };
 static_assert(sizeof(FacHdr) == 8, "FacHdr layout");
 
+#ifndef __CUDACC_RTC__
 struct Pass {
     uint32_t level;
     uint32_t ibeg, iend;          // instruction range (global instruction list)
@@ -175,6 +192,8 @@ struct Level {
     std::vector<uint8_t> perm;    // logical qubit -> physical bit after this level
 };
 
+#endif  // __CUDACC_RTC__
+
 // Measurement layout of the final pass: outcome y (logical) is grouped in blocks
 // of 2^gamma consecutive values whose low gamma logical bits all lie in the tile.
 struct SamplerLayout {
@@ -187,6 +206,7 @@ struct SamplerLayout {
     int8_t rank_of_logical[32];    // rank within the tile, or -1 if the bit is not in the tile
 };
 
+#ifndef __CUDACC_RTC__
 struct PlanHost {
     uint32_t n;
     tqs_precision prec;
@@ -253,7 +273,11 @@ struct NoiseLaunch {
 };
 int launch_noise(const NoiseLaunch &a, void *stream);
 
+#endif  // __CUDACC_RTC__
+
 enum PassMode { MODE_STORE = 0, MODE_SUMS = 1, MODE_SAMPLE = 2 };
+
+#ifndef __CUDACC_RTC__
 
 struct PassLaunch {
     int mode;
@@ -295,8 +319,11 @@ struct PassLaunch {
     double *ksum;
     const void *kmat;          // [slot][8] complex in the state's precision (2x2 on p0, 2x2 on p1)
     uint32_t knq, kp0, kp1;
+    void *spec_fn;             // a kernel specialised for this pass and mode (specialize.h), or nullptr
 };
+#endif  // __CUDACC_RTC__
 constexpr uint32_t kDbgBounds = 1u, kDbgFaultTimeout = 2u;
+#ifndef __CUDACC_RTC__
 int launch_pass(const PassLaunch &a, void *stream);
 
 // The damping choices after one gate for `nnodes` nodes: sums the per-tile
@@ -323,5 +350,6 @@ int launch_fill_u64(unsigned long long *p, uint64_t n, void *stream);
 // ideal: stored physical-order ideal state; perm: logical -> physical.
 int launch_fidelity(const void *ideal, int fp64, const unsigned long long *counts, uint32_t n,
                     const uint8_t *perm_dev, uint64_t shots, double *out3, void *stream);
+#endif  // __CUDACC_RTC__
 
 }  // namespace tqs

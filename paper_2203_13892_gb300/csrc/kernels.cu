@@ -17,6 +17,7 @@
 
 #include "device_common.cuh"
 #include "pass_kernel.h"
+#include "specialize.h"
 
 namespace tqs {
 
@@ -179,6 +180,8 @@ int launch_pass(const PassLaunch &a, void *stream)
     const uint64_t tiles = (uint64_t)1 << (a.n - a.t);
     dim3 grid = a.mode == MODE_SAMPLE ? dim3(a.nnodes) : dim3((unsigned)tiles, a.nnodes);
     cudaStream_t st = (cudaStream_t)stream;
+    if (a.spec_fn && !a.fp64 && !k.fused_k)
+        return spec_launch(a.spec_fn, &k, grid.x, grid.y, smem, stream);
     if (a.fp64) {
         if (a.mode == MODE_STORE) return launch_pass_r<double, MODE_STORE>(k, logr, grid, smem, st);
         if (a.mode == MODE_SUMS) return launch_pass_r<double, MODE_SUMS>(k, logr, grid, smem, st);

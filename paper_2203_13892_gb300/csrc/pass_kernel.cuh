@@ -15,9 +15,11 @@
 // qubits Q acts on phi with U conjugated by the mask bits of Q
 // (U'[r][c] = U[r ^ mu][c ^ mu]); no Pauli ever moves data.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 
 #include <atomic>
+#endif
 
 #include "device_common.cuh"
 #include "pass_kernel.h"
@@ -722,7 +724,17 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
     using C = typename CT<R>::T;
     constexpr int NR = 1 << LOGR;
     extern __shared__ __align__(16) unsigned char smem[];
-    const uint32_t TE = 1u << a.t;
+#ifdef TQS_SPEC
+    // a kernel specialised for one pass: its tile layout is a compile-time constant
+    constexpr uint32_t kT = spec::kT, kN = spec::kN;
+#define TQS_TBIT(j) spec::tbit(j)
+#define TQS_HBIT(b) spec::hbit(b)
+#else
+    const uint32_t kT = a.t, kN = a.n;
+#define TQS_TBIT(j) ((uint32_t)a.tbits[j])
+#define TQS_HBIT(b) ((uint32_t)a.hbits[b])
+#endif
+    const uint32_t TE = 1u << kT;
     C *s = reinterpret_cast<C *>(smem);
     uint16_t *lut = reinterpret_cast<uint16_t *>(s + (TE < (uint32_t)kThreads ? (uint32_t)kThreads : TE));
     double *red = reinterpret_cast<double *>(lut + 256);
@@ -774,16 +786,17 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
 
     // physical offsets: thread bits (tile positions 0..7) and slot bits (8..t-1)
     uint32_t tphys = 0;
-    const uint32_t tb = a.t < 8u ? a.t : 8u;
+    const uint32_t tb = kT < 8u ? kT : 8u;
+#pragma unroll
     for (uint32_t j = 0; j < tb; j++)
-        tphys |= ((tid >> j) & 1u) << a.tbits[j];
+        tphys |= ((tid >> j) & 1u) << TQS_TBIT(j);
     // physical offsets of the register slots (uniform), kept in shared memory
     uint32_t *soff = reinterpret_cast<uint32_t *>(shu + 4);
     if (tid < (uint32_t)NR) {
         uint32_t o = 0;
         for (int b = 0; b < LOGR; b++)
             if ((tid >> b) & 1u)
-                o |= 1u << a.tbits[8 + b];
+                o |= 1u << TQS_TBIT(8 + b);
         soff[tid] = o;
     }
 
@@ -833,9 +846,10 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
     double resid = 0.0;
     if (MODE != MODE_SAMPLE) {
         const uint32_t h = blockIdx.x;
-        for (uint32_t b = 0; b < a.n - a.t; b++)
+#pragma unroll
+        for (uint32_t b = 0; b < kN - kT; b++)
             if ((h >> b) & 1u)
-                base |= 1u << a.hbits[b];
+                base |= 1u << TQS_HBIT(b);
     } else {
         // stage 1: the block of 2^gamma outcomes, from this leaf's block sums
         const double *Sl = a.S + (uint64_t)slot * SL.groups;
@@ -920,7 +934,7 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
         uint32_t m = 0;
 #pragma unroll
         for (int b = 0; b < LOGR; b++)
-            m |= ((mask >> a.tbits[8 + b]) & 1u) << b;
+            m |= ((mask >> TQS_TBIT(8 + b)) & 1u) << b;
         return m;
     };
     auto flush = [&]() {
@@ -1204,6 +1218,15 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
         }
     };
     constexpr uint32_t CS = (uint32_t)sizeof(C);
+#ifdef TQS_SPEC
+    // the pass's records as straight-line code (generated from the same program)
+    if (!zero_tile) {
+        __syncthreads();  // the staged noise bytes
+#include "tqs_spec_walk.inc"
+    } else {
+        mask = m1.mask;
+    }
+#else
     if (!zero_tile) {
         for (uint32_t c = a.chunk_begin; c < a.chunk_end; c++) {
             const uint32_t o0 = a.chunk_off[c], o1 = a.chunk_off[c + 1];
@@ -1457,6 +1480,7 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
     } else {
         mask = m1.mask;
     }
+#endif
     if (FUSE && a.fused_k) {  // every path reaches here: free the tensor memory
         tc_fence_before();
         __syncthreads();
@@ -1513,8 +1537,9 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
     }
     // tile-coordinate frame mask (final frame)
     uint32_t mT = 0;
-    for (uint32_t j = 0; j < a.t; j++)
-        mT |= ((mask >> a.tbits[j]) & 1u) << j;
+#pragma unroll
+    for (uint32_t j = 0; j < kT; j++)
+        mT |= ((mask >> TQS_TBIT(j)) & 1u) << j;
     if (MODE == MODE_SAMPLE) {
         __syncthreads();
         if (active) {
@@ -1539,7 +1564,7 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
         // as FP64.  The index map is linear over XOR: thread part ^ slot part.
         uint32_t Lt = 0;
         {
-            const uint32_t et = tid ^ (mT & 0xffu), tb = a.t < 8u ? a.t : 8u;
+            const uint32_t et = tid ^ (mT & 0xffu), tb = kT < 8u ? kT : 8u;
             for (uint32_t j = 0; j < tb; j++)
                 Lt |= ((et >> j) & 1u) << lut[j];
         }
@@ -1568,8 +1593,9 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
             }
         }
         uint64_t hpart = 0;
-        for (uint32_t b = 0; b < a.n - a.t; b++) {
-            const uint32_t pb = a.hbits[b];
+#pragma unroll
+        for (uint32_t b = 0; b < kN - kT; b++) {
+            const uint32_t pb = TQS_HBIT(b);
             hpart |= (uint64_t)(((base ^ mask) >> pb) & 1u) << (SL.logical_of_hbit[b] - SL.gamma);
         }
         const uint32_t gam = SL.gamma, B = 1u << gam;
@@ -1647,6 +1673,10 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
     }
 }
 
+#undef TQS_TBIT
+#undef TQS_HBIT
+
+#ifndef __CUDACC_RTC__
 template <typename R, int MODE, int LOGR, bool FUSE> static int set_pass_attr()
 {
     return (int)cudaFuncSetAttribute(pass_kernel<R, MODE, LOGR, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1703,5 +1733,6 @@ int launch_pass_r(const PassK &k, int logr, dim3 grid, size_t smem, cudaStream_t
     default: return launch_pass_t<R, MODE, 5, false>(k, grid, smem, st);
     }
 }
+#endif  // __CUDACC_RTC__
 
 }  // namespace tqs

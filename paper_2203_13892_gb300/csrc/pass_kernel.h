@@ -3,7 +3,9 @@
 // translation unit (pass_f32_store.cu ... pass_f64_sample.cu) so that the
 // kernel's instantiations compile in parallel.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 
 #include "internal.h"
 
@@ -40,11 +42,13 @@ struct PassK {
     SamplerLayout samp;
 };
 
+#ifndef __CUDACC_RTC__
 // Launch the pass kernel of element type R (float or double) and mode MODE
 // (MODE_STORE, MODE_SUMS or MODE_SAMPLE) for tile width 2^(8 + logr).
 template <typename R, int MODE>
 int launch_pass_r(const PassK &k, int logr, dim3 grid, size_t smem, cudaStream_t st);
 // Raise the dynamic shared-memory limit of every instantiation of (R, MODE).
 template <typename R, int MODE> int set_attrs_r();
+#endif
 
 }  // namespace tqs

@@ -75,6 +75,10 @@ extern "C" tqs_status tqs_simulate_static(const tqs_circuit *c, const tqs_noise 
         return tqs::set_error(TQS_EUNSUPPORTED,
                               "the learned partitioner allocates device memory for its network; "
                               "tqs_simulate_static takes DCP, UCP, XCP or an explicit tree");
+    if (o.flags & TQS_FLAG_SPECIALIZE)
+        return tqs::set_error(TQS_EUNSUPPORTED,
+                              "specialised pass kernels are compiled and loaded when a plan is created; "
+                              "tqs_simulate_static takes the generic kernels");
     o.workspace = nullptr;  // the scratch is the static array
     o.workspace_bytes = 0;
     o.flags &= ~TQS_FLAG_PROFILE;  // no events are created on this path
