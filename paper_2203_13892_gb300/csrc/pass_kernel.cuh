@@ -729,10 +729,12 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
     constexpr uint32_t kT = spec::kT, kN = spec::kN;
 #define TQS_TBIT(j) spec::tbit(j)
 #define TQS_HBIT(b) spec::hbit(b)
+#define TQS_SOFF(k) spec::soff(k)
 #else
     const uint32_t kT = a.t, kN = a.n;
 #define TQS_TBIT(j) ((uint32_t)a.tbits[j])
 #define TQS_HBIT(b) ((uint32_t)a.hbits[b])
+#define TQS_SOFF(k) soff[k]
 #endif
     const uint32_t TE = 1u << kT;
     C *s = reinterpret_cast<C *>(smem);
@@ -887,7 +889,7 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
         const uint32_t tb0 = base | tphys;
 #pragma unroll
         for (int k = 0; k < NR; k++) {
-            const uint32_t ph = tb0 | soff[k];
+            const uint32_t ph = tb0 | TQS_SOFF(k);
             if (!active)
                 v[k] = mk((R)0, (R)0);
             else if (synth)
@@ -1500,7 +1502,7 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
             const uint32_t tb0 = base | tphys;
 #pragma unroll
             for (int k = 0; k < NR; k++) {
-                const uint32_t lg = (tb0 | soff[k]) ^ mask;
+                const uint32_t lg = (tb0 | TQS_SOFF(k)) ^ mask;
                 const uint32_t ix = ((lg >> a.kp0) & 1u) | (a.knq == 2 ? ((lg >> a.kp1) & 1u) << 1 : 0u);
                 const double w = (double)norm2<R>(v[k]);
                 s4[0] += ix == 0 ? w : 0.0;
@@ -1531,7 +1533,7 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
             const uint32_t tb0 = base | tphys;
 #pragma unroll
             for (int k = 0; k < NR; k++)
-                dst[tb0 | soff[k]] = v[k];
+                dst[tb0 | TQS_SOFF(k)] = v[k];
         }
         return;
     }
@@ -1554,6 +1556,114 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
         return ((uint32_t)lut[key & 127] | (uint32_t)lut[128 + ((key >> 7) & 127)]) ^ mT;
     };
 
+#ifdef TQS_SPEC
+    if constexpr (MODE == MODE_SUMS && sizeof(R) == 4) {
+        // Block sums of |a|^2 (FP32 states), reduced where the amplitudes live.  A
+        // block is the 2^gamma outcomes that share every logical bit above gamma;
+        // its in-tile bits are the tile positions of logical ranks 0..gamma-1,
+        // each a register slot, a lane bit or a warp bit of this layout.  So the
+        // block sum is a sum over those slots (adds between registers), those
+        // lanes (shuffles) and those warps (shared memory); the thread whose
+        // in-block thread bits are 0 then writes one FP64 sum per combination of
+        // the other slots.  The frame mask does not change which amplitudes share
+        // a block, only the block's index (logical = physical ^ frame).
+        uint32_t in_slot = 0, in_thr = 0;
+        for (uint32_t r = 0; r < SL.gamma; r++) {
+            const uint32_t j = SL.rank_pos[r];
+            if (j >= 8u)
+                in_slot |= 1u << (j - 8u);
+            else
+                in_thr |= 1u << j;
+        }
+        float w[NR];
+#pragma unroll
+        for (int k = 0; k < NR; k++)
+            w[k] = active ? norm2<R>(v[k]) : 0.0f;
+#pragma unroll
+        for (int sb = 0; sb < LOGR; sb++) {
+            if (!((in_slot >> sb) & 1u))
+                continue;
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                if (!((k >> sb) & 1))
+                    w[k] += w[k | (1 << sb)];
+        }
+        // live partials: registers whose in-block slot bits are all 0
+        const uint32_t in_lane = in_thr & 31u, in_warp = in_thr & ~31u;
+        for (uint32_t l = 0; l < 5u; l++) {
+            if (!((in_lane >> l) & 1u))
+                continue;
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                if (((uint32_t)k & in_slot) == 0u)
+                    w[k] += __shfl_xor_sync(0xffffffffu, w[k], 1 << l);
+        }
+        if (in_warp) {
+            float *sp = reinterpret_cast<float *>(s);  // the tile region: kThreads x NR floats
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < NR; k++)
+                if (((uint32_t)k & in_slot) == 0u)
+                    sp[(uint32_t)k * kThreads + tid] = w[k];
+            __syncthreads();
+            if ((tid & in_warp) == 0u) {
+#pragma unroll
+                for (int k = 0; k < NR; k++) {
+                    if (((uint32_t)k & in_slot) != 0u)
+                        continue;
+                    float acc = 0.0f;
+                    // every subset of the in-block warp bits, in a fixed order
+                    for (uint32_t sub = in_warp;; sub = (sub - 1u) & in_warp) {
+                        acc += sp[(uint32_t)k * kThreads + (tid | sub)];
+                        if (sub == 0u)
+                            break;
+                    }
+                    w[k] = acc;
+                }
+            }
+        }
+        if (active && (tid & in_thr) == 0u) {
+            uint64_t hpart = 0;
+            for (uint32_t b = 0; b < kN - kT; b++) {
+                const uint32_t pb = TQS_HBIT(b);
+                hpart |= (uint64_t)(((base ^ mask) >> pb) & 1u) << (SL.logical_of_hbit[b] - SL.gamma);
+            }
+            // the logical tile bits above gamma: this thread's part, the frame's
+            // part on the slots, and per slot the block-index bit it sets
+            uint64_t g0 = hpart;
+            uint32_t dsh[LOGR > 0 ? LOGR : 1];
+#pragma unroll
+            for (int sb = 0; sb < LOGR; sb++)
+                dsh[sb] = 63u;  // an in-block slot: never used
+            const uint32_t et = tid ^ mT;
+            for (uint32_t r = SL.gamma; r < kT; r++) {
+                const uint32_t j = SL.rank_pos[r], sh = SL.rank_q[r] - SL.gamma;
+                if (j < 8u) {
+                    g0 |= (uint64_t)((et >> j) & 1u) << sh;
+                } else {
+                    g0 |= (uint64_t)((mT >> j) & 1u) << sh;
+#pragma unroll
+                    for (int sb = 0; sb < LOGR; sb++)
+                        if ((uint32_t)sb == j - 8u)
+                            dsh[sb] = sh;
+                }
+            }
+            double *Srow = a.S + (uint64_t)slot * SL.groups;
+#pragma unroll
+            for (int k = 0; k < NR; k++) {
+                if (((uint32_t)k & in_slot) != 0u)
+                    continue;
+                uint64_t g = g0;
+#pragma unroll
+                for (int sb = 0; sb < LOGR; sb++)
+                    if ((k >> sb) & 1)
+                        g ^= (uint64_t)1 << dsh[sb];
+                Srow[g] = (double)w[k];
+            }
+        }
+        return;
+    }
+#endif
     if (MODE == MODE_SUMS) {
         // Block sums of |a|^2 over the 2^gamma outcomes that share every logical
         // bit above gamma.  Each |a|^2 is staged in shared memory at its logical
@@ -1675,6 +1785,7 @@ __global__ void __launch_bounds__(kThreads, FUSE ? 2
 
 #undef TQS_TBIT
 #undef TQS_HBIT
+#undef TQS_SOFF
 
 #ifndef __CUDACC_RTC__
 template <typename R, int MODE, int LOGR, bool FUSE> static int set_pass_attr()

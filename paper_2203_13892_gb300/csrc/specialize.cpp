@@ -194,7 +194,12 @@ std::string spec_generate(const PlanHost &H, const Pass &ps, int mode, SpecSourc
         d << "__host__ __device__ constexpr uint32_t hbit(uint32_t b) { return ";
         for (uint32_t b = 0; b < H.n - ps.t; b++)
             d << "b == " << b << "u ? " << (uint32_t)ps.hbits[b] << "u : ";
-        d << "0u; }\n} }\n";
+        d << "0u; }\n";
+        // physical offset of register slot k: its bits deposited at the slot positions' physical bits
+        d << "__host__ __device__ constexpr uint32_t soff(uint32_t k) { return 0u";
+        for (int b = 0; b < out.logr; b++)
+            d << " | (((k >> " << b << ") & 1u) << " << (uint32_t)ps.tbits[8 + b] << ")";
+        d << "; }\n} }\n";
         out.defs = d.str();
     }
     std::ostringstream o;

@@ -4,13 +4,15 @@ headline one (which bench.py measures): one JSON line per configuration.
     python -m paper_2203_13892_gb300.perf [--config NAME ...] [--reps K]
 
   qft16 / rc16   16-qubit QFT and random 16x40 circuit, 8,192 shots, tree FP32
-                 (DCP), beside plain baseline mode in FP64 on the same GPU
+                 (DCP) with the specialised and with the generic pass kernels,
+                 beside plain baseline mode in FP64 on the same GPU
   batch64        64 random circuits, 12-22 qubits, 20-60 layers, 2,048 shots
                  each, one captured CUDA graph replayed (FP32, DCP trees),
                  optionally autotuned (--autotune)
   qft26 / rc26   26-qubit QFT (32,768 shots) and random 26x30 circuit (2,048
                  shots: its ~30 passes per level make 32,768 shots a minutes-long
-                 run), 512 MiB FP32 states, tree FP32 (DCP)
+                 run), 512 MiB FP32 states, tree FP32 (DCP), specialised and
+                 generic pass kernels
   qft20_host     the 20-qubit QFT, 32,000 shots, tree FP32, with the state pool
                  in device memory and in mapped host memory (not in the default
                  list)
@@ -41,13 +43,20 @@ def _device_counts(n):
     return torch.zeros(1 << n, dtype=torch.int64, device="cuda")
 
 
-def single(name, circ, shots, reps, modes=(("tree", "fp32"), ("baseline", "fp64"))):
+SPEC_AND_GENERIC = (("tree", "fp32", True), ("tree", "fp32", False), ("baseline", "fp64", False))
+
+
+def single(name, circ, shots, reps, modes=SPEC_AND_GENERIC):
+    """Each mode is (tree or baseline, precision, specialised pass kernels)."""
     c, nz = capi.circuit(circ), capi.tqs_noise_model(*NOISE)
     d = _device_counts(circ.n)
     out = {"config": name, "n": circ.n, "gates": len(circ.gates), "shots": shots}
-    for mode, prec in modes:
+    for mode, prec, spec in modes:
         sh = shots if mode == "tree" else max(64, shots // 16)
-        plan = capi.tqs_plan_create(c, nz, sh, capi.options(mode=mode, prec=prec, flags=capi.TQS_FLAG_PROFILE))
+        flags = capi.TQS_FLAG_PROFILE | (capi.TQS_FLAG_SPECIALIZE if spec else 0)
+        t0 = time.perf_counter()
+        plan = capi.tqs_plan_create(c, nz, sh, capi.options(mode=mode, prec=prec, flags=flags))
+        create_s = time.perf_counter() - t0
         capi.tqs_plan_execute(plan, 0, d.data_ptr())
         ms = []
         for r in range(reps):
@@ -55,8 +64,9 @@ def single(name, circ, shots, reps, modes=(("tree", "fp32"), ("baseline", "fp64"
             ms.append(rep["kernel_ms"])
         plan.close()
         best = min(ms)
-        out[f"{mode}_{prec}"] = {
+        out[f"{mode}_{prec}" + ("_spec" if spec else "")] = {
             "shots": sh, "ms": best, "shots_per_s": sh / (best * 1e-3), "tree": rep["arity"],
+            "plan_create_s": round(create_s, 2),
             "passes": rep["passes"], "theo_speedup": rep["theo_speedup"],
             "classes_ms": {k: v["ms"] for k, v in rep["prof"].items() if v["launches"]},
             "classes_alg_GBps": {k: v["bytes"] / (v["ms"] * 1e-3) / 1e9 for k, v in rep["prof"].items()
@@ -64,6 +74,9 @@ def single(name, circ, shots, reps, modes=(("tree", "fp32"), ("baseline", "fp64"
         }
     if "tree_fp32" in out and "baseline_fp64" in out:
         out["tree_fp32_over_baseline_fp64"] = out["tree_fp32"]["shots_per_s"] / out["baseline_fp64"]["shots_per_s"]
+    if "tree_fp32_spec" in out and "baseline_fp64" in out:
+        out["tree_fp32_spec_over_baseline_fp64"] = (out["tree_fp32_spec"]["shots_per_s"] /
+                                                    out["baseline_fp64"]["shots_per_s"])
     return out
 
 
@@ -170,9 +183,9 @@ def main(argv=None):
         elif name == "rc16":
             r = single(name, random_layers(16, 40, 16040), 8192, a.reps)
         elif name == "qft26":
-            r = single(name, qft(26), 32768, 1, modes=(("tree", "fp32"),))
+            r = single(name, qft(26), 32768, 1, modes=(("tree", "fp32", True), ("tree", "fp32", False)))
         elif name == "rc26":
-            r = single(name, random_layers(26, 30, 26030), 2048, 1, modes=(("tree", "fp32"),))
+            r = single(name, random_layers(26, 30, 26030), 2048, 1, modes=(("tree", "fp32", True), ("tree", "fp32", False)))
         elif name == "qft20_host":
             r = host_pool(name, qft(20), 32000, a.reps)
         elif name == "batch64":
