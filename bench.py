@@ -67,8 +67,8 @@ def kernel_source_hash(kernels="generic"):
     """Hash of the files the pass kernel is compiled and launched from: its six
     instantiation units, the headers of csrc they include, and kernels.cu (which
     sets its grid and shared memory); for the specialised kernels also the
-    generator that writes their statements (specialize.cpp).  Host-only sources
-    do not enter."""
+    generator that writes their statements (specialize.cpp and its header).
+    Host-only sources (the NVRTC / driver runtime among them) do not enter."""
     d = os.path.join(ROOT, "paper_2203_13892_gb300", "csrc")
     names = sorted(f for f in os.listdir(d) if f.startswith("pass_") and f.endswith(".cu"))
     names += ["pass_kernel.cuh", "pass_kernel.h", "device_common.cuh", "internal.h", "kernels.cu"]

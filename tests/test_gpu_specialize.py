@@ -130,3 +130,21 @@ def test_metric_workload_specialized(orc):
     got = tqs.tqs_debug_node_state(c, nz, SHOTS, 5, o, L - 1, 31999, N)
     want = orc.core.node_state(circ, P1, P2, 5, arity, split, L - 1, 31999)
     assert np.max(np.abs(got - want)) < 2e-5
+
+
+def test_batch_graph_with_specialised_kernels():
+    """A batch of uneven circuits captured in one CUDA graph with the specialised
+    kernels (driver-API launches inside the capture) gives the histograms of the
+    single simulations with the same kernels, replay after replay."""
+    circs = [random_layers(6, 5, 1), qft(9), random_layers(13, 7, 2), qft(4)]
+    shots = [300, 1000, 700, 64]
+    handles = [tqs.circuit(c) for c in circs]
+    noises = [tqs.tqs_noise_model(P1, P2, PM) for _ in circs]
+    b = tqs.tqs_batch_create(handles, noises, shots, tqs.options(prec="fp32", flags=SPEC))
+    for seeds in ([1, 2, 3, 4], [40, 30, 20, 10]):
+        tqs.tqs_batch_execute(b, seeds)
+        for i, c in enumerate(circs):
+            got = tqs.tqs_batch_counts(b, i, c.n)
+            want, _, _ = tqs.tqs_simulate(handles[i], noises[i], shots[i], seeds[i],
+                                          tqs.options(prec="fp32", flags=SPEC | capi.TQS_FLAG_NO_FIDELITY), n=c.n)
+            assert np.array_equal(got, want), (i, seeds[i])
