@@ -148,3 +148,23 @@ def test_batch_graph_with_specialised_kernels():
             want, _, _ = tqs.tqs_simulate(handles[i], noises[i], shots[i], seeds[i],
                                           tqs.options(prec="fp32", flags=SPEC | capi.TQS_FLAG_NO_FIDELITY), n=c.n)
             assert np.array_equal(got, want), (i, seeds[i])
+
+
+def test_index_checks_in_specialised_kernels():
+    """TQS_FLAG_DEBUG_BOUNDS reaches the specialised kernels (their prologue is the
+    generic one): valid input changes nothing, an understated output pool is caught
+    before any access (TQS_EBOUNDS), and the next call is correct."""
+    circ = qft(10)
+    c, nz = tqs.circuit(circ), tqs.tqs_noise_model(P1, P2, PM)
+    base = capi.TQS_FLAG_NO_FIDELITY | SPEC
+    o = dict(prec="fp32", batch=4)
+    want, _, _ = tqs.tqs_simulate(c, nz, 256, 5, tqs.options(flags=base, **o), n=circ.n)
+    checked, _, _ = tqs.tqs_simulate(c, nz, 256, 5, tqs.options(flags=base | capi.TQS_FLAG_DEBUG_BOUNDS, **o),
+                                     n=circ.n)
+    assert np.array_equal(checked, want)
+    with pytest.raises(capi.TqsError) as e:
+        tqs.tqs_simulate(c, nz, 256, 5, tqs.options(flags=base | capi.TQS_FLAG_DEBUG_BOUNDS |
+                                                     capi.TQS_FLAG_FAULT_BOUNDS, **o), n=circ.n)
+    assert e.value.status == capi.TQS_EBOUNDS
+    again, _, _ = tqs.tqs_simulate(c, nz, 256, 5, tqs.options(flags=base, **o), n=circ.n)
+    assert np.array_equal(again, want)

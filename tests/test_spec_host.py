@@ -112,3 +112,33 @@ def test_refusals():
     with pytest.raises(capi.TqsError) as e:
         tqs.tqs_debug_spec_source(c, nz, 64, tqs.options(prec="fp32"), 0, 3)
     assert e.value.status == capi.TQS_EINVAL
+
+
+def test_test_plans_reach_every_record_form():
+    """The plans the GPU parity tests run with specialised kernels produce every
+    form the generator writes: real and complex one-qubit matrices, 4x4
+    matrices, base, slot and pair phase terms, the per-gate fallback of runs,
+    damping records."""
+    def all_sources(circ, nz, shots, o):
+        _, _, tiles = tqs.tqs_debug_plan_order(tqs.circuit(circ), nz, shots, o, len(circ.gates))
+        return "".join(tqs.tqs_debug_spec_source(tqs.circuit(circ), nz, shots, o, p, 0) for p in range(len(tiles)))
+
+    from test_gpu_parity import mixed_circuit
+
+    nz = tqs.tqs_noise_model(0.15, 0.3, 0.0)
+    src = ""
+    for tile in (8, 10, 12):
+        circ = mixed_circuit(13, 5)
+        o = tqs.options(prec="fp32", tile_qubits=tile, arity=[4, 2, 2, 2],
+                        split=[0, 20, 61, 100, len(circ.gates)])
+        src += all_sources(circ, nz, 32, o)
+    for form in ("dense1_real(", "dense1(", "dense2(", "acc.base += add", "acc.E[", "acc.Gs[", "acc_alpha(",
+                 "acc_gamma(", "apply_noise("):
+        assert form in src, form
+    circ = random_layers(10, 4, 77)
+    circ.add("h", 0).add("cx", 0, 9).add("cp", 3, 5, 0.4).add("swap", 2, 7).add("x", 4)
+    G = len(circ.gates)
+    nzk = tqs.tqs_noise_model_ex(*P, ad_gamma=0.01, pd_lambda=0.01, t1=50e-6, t2=70e-6, time_1q=0.5e-6,
+                                 time_2q=2e-6)
+    o = tqs.options(prec="fp32", tile_qubits=8, arity=[40, 3, 5], split=[0, G // 3, 2 * G // 3, G])
+    assert "km[0].x" in all_sources(circ, nzk, 600, o)
