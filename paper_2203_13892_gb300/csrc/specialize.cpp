@@ -62,8 +62,15 @@ void emit_noise(std::ostringstream &o, uint32_t site, uint32_t npaulis, uint32_t
 // One FP32 diagonal run (RunHdr32 layout), as the interpreter walks it: the
 // grouped phase entries when no Pauli of this node falls inside the run, else
 // gate by gate from the run's gate entries.
-bool emit_run(std::ostringstream &o, const RecHdr &h, const uint8_t *pay, int logr, uint32_t &len, std::string &why)
+// `avail` = the bytes of the chunk from the record's header on: the record's
+// length (from its header) is checked against it before any entry is read.
+bool emit_run(std::ostringstream &o, const RecHdr &h, const uint8_t *pay, uint32_t avail, int logr, uint32_t &len,
+              std::string &why)
 {
+    if (avail < 96u || h.iend < h.ibeg) {
+        why = "truncated run record";
+        return false;
+    }
     RunHdr32 rh;
     std::memcpy(&rh, pay, sizeof rh);
     const uint32_t nent = rh.pad[1];
@@ -73,6 +80,10 @@ bool emit_run(std::ostringstream &o, const RecHdr &h, const uint8_t *pay, int lo
     const uint8_t *en = pay + 80;
     const uint8_t *gents = pay + 80 + ent_bytes;
     len = 96u + ent_bytes + ngates * ES;
+    if ((uint64_t)96u + ent_bytes + (uint64_t)ngates * ES > avail) {
+        why = "run record runs past its chunk";
+        return false;
+    }
     uint32_t nsum = rh.nbase;
     for (int q = 0; q < logr; q++)
         nsum += rh.ne[q];
@@ -170,7 +181,7 @@ std::string spec_generate(const PlanHost &H, const Pass &ps, int mode, SpecSourc
         return "only FP32 states have specialised kernels";
     if (ps.fused_blocks)
         return "the pass holds fused tensor-core blocks";
-    if (ps.t > (uint32_t)kMaxTile || ps.t + 0u > H.n)
+    if (ps.t > (uint32_t)kMaxTile || ps.t > H.n)
         return "tile wider than the state";
     out = SpecSource{};
     out.mode = mode;
@@ -221,7 +232,13 @@ std::string spec_generate(const PlanHost &H, const Pass &ps, int mode, SpecSourc
             }
             if (h.type != REC_RUN)
                 o << "    flush();\n";
+            // each record's length is checked against the chunk before its payload is read
+            const uint32_t avail = o1 - o0 - p;
             uint32_t len = 0;
+            if (h.type == REC_DENSE1 && avail < 48u)
+                return "truncated one-qubit gate record";
+            if (h.type == REC_DENSE2 && avail < 16u + 16u * 8u)
+                return "truncated two-qubit gate record";
             if (h.type == REC_DENSE1) {
                 float u[8];
                 std::memcpy(u, pay, sizeof u);
@@ -258,13 +275,11 @@ std::string spec_generate(const PlanHost &H, const Pass &ps, int mode, SpecSourc
                 len = 16;
             } else if (h.type == REC_RUN) {
                 std::string why;
-                if (o1 - o0 - p < 96 || !emit_run(o, h, pay, out.logr, len, why))
-                    return why.empty() ? std::string("truncated run record") : why;
+                if (!emit_run(o, h, pay, avail, out.logr, len, why))
+                    return why;
             } else {
                 return "record type " + std::to_string((int)h.type) + " has no specialised form";
             }
-            if (len > o1 - o0 - p)
-                return "record runs past its chunk";
             p += len;
         }
     }
