@@ -199,7 +199,12 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
     for (auto &lv : H.levels)
         maxact = std::max<uint64_t>(maxact, lv.active);
     const uint64_t tiles = (uint64_t)1 << (H.n - std::min<uint32_t>(H.n, H.tile_max));
-    uint64_t want = o.batch ? o.batch : std::max<uint64_t>(64, 65536 / tiles);
+    // nodes per launch: about 2^18 tiles per level launch, so that the
+    // one-CTA-per-leaf sample pass and the per-level noise launches fill the GPU
+    // (2^16 with the pool in pinned host memory, which grows with the batch);
+    // the memory budget below caps it
+    const uint64_t tiles_per_launch = (o.flags & TQS_FLAG_HOST_POOL) ? 65536 : 262144;
+    uint64_t want = o.batch ? o.batch : std::max<uint64_t>(64, tiles_per_launch / tiles);
     want = std::min<uint64_t>(want, 65535);
     want = std::min<uint64_t>(want, maxact);
     const uint32_t L = (uint32_t)H.levels.size();
