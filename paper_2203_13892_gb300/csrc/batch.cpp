@@ -251,7 +251,9 @@ tqs_status tqs_batch_create(size_t count, const tqs_circuit *const *circuits, co
         oi.workspace = nullptr;
         oi.workspace_bytes = (size_t)(budget * std::ldexp(1.0, (int)circuits[i]->c.n) / wsum);
         std::unique_ptr<tqs_plan> p;
-        tqs_status st = tqs::make_plan(circuits[i], noises[i], shots[i], oi, false, p);
+        // the batch's plans share the device and run concurrently: each keeps the
+        // smaller launches of 2^16 tiles by default
+        tqs_status st = tqs::make_plan(circuits[i], noises[i], shots[i], oi, false, p, 65536);
         if (st != TQS_OK)
             return st;
         b->plans.push_back(std::move(p));

@@ -41,7 +41,7 @@ tqs_options opts_or_default(const tqs_options *o)
 }
 
 tqs_status make_plan_once(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options &o,
-                          bool store_leaves, std::unique_ptr<tqs_plan> &out)
+                          bool store_leaves, std::unique_ptr<tqs_plan> &out, uint64_t launch_tiles = 0)
 {
     if (!c || !nz)
         return fail(TQS_EINVAL, "circuit and noise handles are required");
@@ -62,6 +62,7 @@ tqs_status make_plan_once(const tqs_circuit *c, const tqs_noise *nz, uint64_t sh
     if (st != TQS_OK)
         return st;
     p->dp.store_leaves = store_leaves;
+    p->dp.launch_tiles = launch_tiles;
     std::string err;
     st = p->dp.create(o, err);
     if (st != TQS_OK)
@@ -143,16 +144,16 @@ tqs_status fidelity(const tqs_circuit *c, uint64_t shots, const unsigned long lo
 tqs_status tqs::set_error(tqs_status s, const std::string &msg) { return fail(s, msg); }
 
 tqs_status tqs::make_plan(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options &o,
-                          bool store_leaves, std::unique_ptr<tqs_plan> &out)
+                          bool store_leaves, std::unique_ptr<tqs_plan> &out, uint64_t launch_tiles)
 {
     if (!(o.flags & TQS_FLAG_AUTOTUNE) || store_leaves)
-        return make_plan_once(c, nz, shots, o, store_leaves, out);
+        return make_plan_once(c, nz, shots, o, store_leaves, out, launch_tiles);
     tqs_options tuned = o;
     tqs_status st = tqs::autotune(c, nz, shots, o, tuned);
     if (st != TQS_OK)
         return st;
     tuned.flags &= ~TQS_FLAG_AUTOTUNE;
-    return make_plan_once(c, nz, shots, tuned, store_leaves, out);
+    return make_plan_once(c, nz, shots, tuned, store_leaves, out, launch_tiles);
 }
 
 extern "C" {

@@ -203,7 +203,8 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
     // one-CTA-per-leaf sample pass and the per-level noise launches fill the GPU
     // (2^16 with the pool in pinned host memory, which grows with the batch);
     // the memory budget below caps it
-    const uint64_t tiles_per_launch = (o.flags & TQS_FLAG_HOST_POOL) ? 65536 : 262144;
+    const uint64_t tiles_per_launch =
+        launch_tiles ? launch_tiles : ((o.flags & TQS_FLAG_HOST_POOL) ? 65536 : 262144);
     uint64_t want = o.batch ? o.batch : std::max<uint64_t>(64, tiles_per_launch / tiles);
     want = std::min<uint64_t>(want, 65535);
     want = std::min<uint64_t>(want, maxact);

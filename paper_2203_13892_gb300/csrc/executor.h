@@ -20,6 +20,7 @@ struct DevicePlan {
     bool caller_counts = false; // the layout reserves no internal histogram and no fidelity scratch
     const uint64_t *seed_dev = nullptr;  // device seed read by the kernels (graph replays)
     uint64_t batch = 0;         // node instances per chunk and level
+    uint64_t launch_tiles = 0;  // default batch target in tiles per launch (0: the library's choice)
     void *ws = nullptr;
     size_t ws_bytes = 0;
     bool own_ws = false;

@@ -30,8 +30,10 @@ namespace tqs {
 // Records `msg` as the calling thread's tqs_last_error() and returns `s`.
 tqs_status set_error(tqs_status s, const std::string &msg);
 // Partition, lower and upload one simulation (store_leaves keeps every level's states).
+// launch_tiles: the default node batch's target in tiles per launch (0: the
+// library's choice for a plan that has the device to itself).
 tqs_status make_plan(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options &o,
-                     bool store_leaves, std::unique_ptr<tqs_plan> &out);
+                     bool store_leaves, std::unique_ptr<tqs_plan> &out, uint64_t launch_tiles = 0);
 // Chooses tile_qubits for the circuit's shape by timing trial runs (cached per shape).
 tqs_status autotune(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options &o,
                     tqs_options &tuned);
