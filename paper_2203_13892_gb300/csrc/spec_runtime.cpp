@@ -60,7 +60,9 @@ const Api &api()
     std::call_once(once, [] {
         static const char *const rtc[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
                                           nullptr};
-        static const char *const drv[] = {"libcuda.so.1", "libcuda.so", nullptr};
+        // the driver's versioned name only: an unversioned libcuda.so on a host
+        // without a driver is the toolkit's link stub
+        static const char *const drv[] = {"libcuda.so.1", nullptr};
         void *hr = open_first(rtc), *hd = open_first(drv);
         if (!hr) {
             a.why = a.why_rtc = "NVRTC (libnvrtc.so.13) could not be opened";
