@@ -142,3 +142,64 @@ def test_test_plans_reach_every_record_form():
                                  time_2q=2e-6)
     o = tqs.options(prec="fp32", tile_qubits=8, arity=[40, 3, 5], split=[0, G // 3, 2 * G // 3, G])
     assert "km[0].x" in all_sources(circ, nzk, 600, o)
+
+
+def test_matrix_literals_are_the_gates_fp32_matrices(orc):
+    """The generator's hexadecimal literals are exact: each one-qubit dense gate's
+    statement holds the FP32 rounding of that gate's matrix (the oracle's FP64
+    matrix, rounded), real ones as dense1_real with the four real parts."""
+    circ = _mixed(13, 5)
+    c, nz = tqs.circuit(circ), tqs.tqs_noise_model(*P)
+    o = tqs.options(prec="fp32", tile_qubits=8)
+    order, pass_of, tiles = tqs.tqs_debug_plan_order(c, nz, 64, o, len(circ.gates))
+    lit = r"(-?0x[0-9a-f.]+p[-+]\d+)f"
+    checked = 0
+    for p in range(len(tiles)):
+        src = tqs.tqs_debug_spec_source(c, nz, 64, o, p, 0)
+        calls = re.findall(r"\b(dense1_real|dense1)\(\d+u, \d+u, (.*?)\);\n", src)
+        gates = [circ.gates[g] for g, q in zip(order, pass_of) if q == p and circ.gates[g][0] in DENSE1]
+        assert len(calls) == len(gates), p
+        for (kind, args), (name, q0, q1, th, mat) in zip(calls, gates):
+            vals = [float.fromhex(x) for x in re.findall(lit, args)]
+            u = orc.core.gate_matrix(name, th, mat).astype(np.complex64).ravel()
+            if kind == "dense1_real":
+                assert np.all(u.imag == 0) and vals == [float(x) for x in u.real], (name, vals)
+            else:
+                want = [float(x) for z in u for x in (z.real, z.imag)]
+                assert vals == want, (name, vals, want)
+            checked += 1
+    assert checked >= 10
+
+
+def test_qft20_leaf_phase_entries_are_the_controlled_phases():
+    """Each diagonal run of the benchmark's leaf pass, as generated, adds for a
+    thread exactly the controlled phases of its CP gates: one entry per gate,
+    mask = the two qubits' bits (no swaps precede them in this pass, so physical
+    = logical), phase = theta / 2 pi in units of 2^-32 turns (to one unit of
+    rounding)."""
+    circ = qft(20)
+    c, nz = tqs.circuit(circ), tqs.tqs_noise_model(*P)
+    o = tqs.options(prec="fp32")
+    order, pass_of, tiles = tqs.tqs_debug_plan_order(c, nz, 32000, o, len(circ.gates))
+    last = len(tiles) - 1
+    src = tqs.tqs_debug_spec_source(c, nz, 32000, o, last, 1)
+    gates = [circ.gates[g] for g, q in zip(order, pass_of) if q == last]
+    runs, cur = [], None
+    for name, q0, q1, th, _ in gates:
+        if name == "h":
+            if cur is not None:
+                runs.append(cur)
+            cur = []
+        elif name == "cp":
+            cur.append((q0, q1, th))
+    if cur:
+        runs.append(cur)
+    blocks = src.split("// diagonal run")[1:]
+    for run, block in zip(runs, blocks):
+        fast = block.split("} else {")[0]
+        got = sorted((int(m, 16), int(ph, 16)) for m, _, ph in
+                     re.findall(r"if \(\(xt & (0x[0-9a-f]+)u\) == (0x[0-9a-f]+)u\) add \+= (0x[0-9a-f]+)u;", fast))
+        want = sorted(((1 << a) | (1 << b), round(th / (2 * np.pi) * 2 ** 32) % 2 ** 32) for a, b, th in run)
+        assert [m for m, _ in got] == [m for m, _ in want]
+        assert all(abs(x - y) <= 1 for (_, x), (_, y) in zip(got, want)), (got, want)
+    assert len(runs) == 5
