@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <limits>
 #include <memory>
 #include <new>
@@ -302,8 +303,8 @@ tqs_status tqs_debug_plan_order(const tqs_circuit *c, const tqs_noise *nz, uint6
     return TQS_OK;
 }
 
-tqs_status tqs_debug_spec_check(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
-                                uint32_t *nkernels_out, uint64_t *src_bytes_out)
+static tqs_status debug_spec_check(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
+                                   uint32_t *nkernels_out, uint64_t *src_bytes_out)
 {
     if (!c || !nz || !nkernels_out)
         return fail(TQS_EINVAL, "NULL argument");
@@ -346,8 +347,8 @@ tqs_status tqs_debug_spec_check(const tqs_circuit *c, const tqs_noise *nz, uint6
     return TQS_OK;
 }
 
-tqs_status tqs_debug_spec_source(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
-                                 uint32_t pass, int mode, char *buf, uint64_t cap, uint64_t *len_out)
+static tqs_status debug_spec_source(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
+                                    uint32_t pass, int mode, char *buf, uint64_t cap, uint64_t *len_out)
 {
     if (!c || !nz || !len_out)
         return fail(TQS_EINVAL, "NULL argument");
@@ -381,6 +382,26 @@ tqs_status tqs_debug_spec_source(const tqs_circuit *c, const tqs_noise *nz, uint
         buf[n] = '\0';
     }
     return TQS_OK;
+}
+
+tqs_status tqs_debug_spec_check(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
+                                uint32_t *nkernels_out, uint64_t *src_bytes_out)
+{
+    try {  // host allocations and compiler threads may throw: nothing crosses the C ABI
+        return debug_spec_check(c, nz, shots, opts, nkernels_out, src_bytes_out);
+    } catch (const std::exception &e) {
+        return fail(TQS_ENOMEM, e.what());
+    }
+}
+
+tqs_status tqs_debug_spec_source(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,
+                                 uint32_t pass, int mode, char *buf, uint64_t cap, uint64_t *len_out)
+{
+    try {
+        return debug_spec_source(c, nz, shots, opts, pass, mode, buf, cap, len_out);
+    } catch (const std::exception &e) {
+        return fail(TQS_ENOMEM, e.what());
+    }
 }
 
 tqs_status tqs_plan_create(const tqs_circuit *c, const tqs_noise *nz, uint64_t shots, const tqs_options *opts,

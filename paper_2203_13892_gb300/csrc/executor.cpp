@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <string>
 
 #include "executor.h"
@@ -313,6 +314,17 @@ tqs_status DevicePlan::create(const tqs_options &o, std::string &err)
 // TQS_FLAG_SPECIALIZE: one kernel per pass program in the store mode, and the
 // leaf's measuring modes for the last pass of the last level, compiled together.
 tqs_status DevicePlan::build_specialized(std::string &err)
+{
+    // host allocations and compiler threads may throw: nothing crosses the C ABI
+    try {
+        return build_specialized_impl(err);
+    } catch (const std::exception &e) {
+        err = std::string("specialised pass kernels: ") + e.what();
+        return TQS_ENOMEM;
+    }
+}
+
+tqs_status DevicePlan::build_specialized_impl(std::string &err)
 {
     const PlanHost &H = host;
     const std::string why = spec_available();

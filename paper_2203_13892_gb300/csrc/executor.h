@@ -60,6 +60,7 @@ struct DevicePlan {
         return i < spec_fn.size() ? spec_fn[i] : nullptr;
     }
     tqs_status build_specialized(std::string &err);
+    tqs_status build_specialized_impl(std::string &err);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // per-launch profiling (TQS_FLAG_PROFILE)
     struct ProfRec { int kind; double bytes; cudaEvent_t a, b; };
